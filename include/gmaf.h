@@ -1,0 +1,185 @@
+/*
+ * gmaf.h - C ABI of the GB300 piston-gap library (GMAF hot path).
+ *
+ * The library computes, for a joint batch of working conditions of an axial
+ * piston pump's piston/bore oil film (arXiv 2511.06824):
+ *   (a) the FVM-discretised Reynolds equation of the unwrapped gap
+ *       (Sec. 2.1, Eq. 2.1-2.7) with film thickness from Eq. 2.3 plus
+ *       dimple texture,
+ *   (b) the solution of all conditions as one joint system (Eq. 3.7-3.8) by
+ *       ASSOR-II (Eq. 3.3-3.6) or Jacobi (Eq. 2.8) preconditioned conjugate
+ *       gradient (Table 1) under the synchronized criterion (Eq. 3.9),
+ *   (c) force and moment integration from normal pressure and viscous shear
+ *       (Sec. 2.4-III),
+ *   and, around them, one double-Jacobian Picard iteration (Eq. 2.12-2.19).
+ *
+ * Conventions shared by every entry point:
+ *   - All functions are `extern "C"`, return an int status (GMAF_OK = 0 or a
+ *     negative code below), never abort and never print.
+ *   - Device arrays are owned by the caller (e.g. torch tensors); the library
+ *     owns only the opaque context and the workspace it allocates inside the
+ *     context's HBM budget.  Host arrays are plain C arrays owned by the
+ *     caller.
+ *   - Grid layout: n_theta x n_z cells, theta (circumferential, periodic) is
+ *     the fastest index; cell (i, j) of condition k is element
+ *     i + n_theta * (j + n_z * k) of a joint array (system-major, Eq. 3.8).
+ *   - Work is issued on the context's CUDA stream.  Calls that return host
+ *     results (iteration counts, residuals, loads of the Picard step)
+ *     synchronise that stream before returning; gmaf_assemble and
+ *     gmaf_integrate_loads are asynchronous.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef GMAF_H
+#define GMAF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GMAF_OK              0
+#define GMAF_INVALID_ARG    -1  /* null pointer, n_theta < 3, n_z < 2, c <= 0, mu <= 0,
+                                   omega not in (0,2), eps <= 0, ...            */
+#define GMAF_CONTACT        -2  /* some film thickness h <= 0 (piston touches the bore) */
+#define GMAF_NOT_CONVERGED  -3  /* iteration budget exhausted; outputs still written   */
+#define GMAF_NONFINITE      -4  /* NaN/Inf met in a reduction (or a non-positive u.Au) */
+#define GMAF_OUT_OF_MEMORY  -5  /* workspace would exceed the context's HBM budget    */
+#define GMAF_CUDA_ERROR     -6  /* CUDA runtime error; destroy the context            */
+#define GMAF_TIMEOUT        -7  /* a device-side bounded loop gave up                 */
+
+/* ---- problem description (Sec. 2.1, Eq. 2.3, Table 8) ---------------- */
+
+/* Cells of the unwrapped gap: n_theta >= 3 around (periodic), n_z >= 2 along. */
+typedef struct { int32_t n_theta, n_z; } gmaf_grid;
+
+/* R_k piston radius [m]; L gap (coupling) length [m]; c radial clearance [m]
+ * (bore radius R_c = R_k + c); mu dynamic viscosity [Pa s]; v_slide axial speed
+ * of the piston relative to the bore, + from chamber (z = 0) to case (z = L)
+ * [m/s]; p_chamber, p_case Dirichlet pressures at z = 0 and z = L [Pa]. */
+typedef struct {
+    double R_k, L, c;
+    double mu;
+    double v_slide;
+    double p_chamber, p_case;
+} gmaf_physics;
+
+/* kind 0: smooth piston.  kind 1: flat-bottom circular dimples of `radius` and
+ * `depth` on a hexagonal lattice with the given area density; the lattice has
+ * a whole number of columns around the piston and is shifted by
+ * (offset_theta, offset_z) metres on the unwrapped surface (h_Text of Eq. 2.3). */
+typedef struct {
+    int32_t kind;
+    double radius, depth, area_density, offset_theta, offset_z;
+} gmaf_texture;
+
+/* Eccentricities e1, e2 at z = 0 and e3, e4 at z = L [m] and their rates [m/s] (Eq. 2.3). */
+typedef struct { double e[4], edot[4]; } gmaf_state;
+
+/* precond: 0 Jacobi (Eq. 2.8), 1 ASSOR-II (Eq. 3.4).  omega in (0, 2).
+ * eps: synchronized criterion ||A_G p_G - S_G||_2 / ||S_G||_2 <= eps (Eq. 3.9).
+ * max_iter: PCG iteration budget (inner iterations in mixed precision).
+ * precision: 0 FP64 throughout; 1 mixed - FP32 stencil, preconditioner and
+ *   vector updates with dot products accumulated to FP64 accuracy, inside an
+ *   FP64 iterative-refinement loop whose residual and stopping test are FP64.
+ * zero_init: 1 start from p = 0 (Table 1 step 1); 0 use the contents of p. */
+typedef struct {
+    int32_t precond;
+    double omega, eps;
+    int32_t max_iter;
+    int32_t precision;
+    int32_t zero_init;
+} gmaf_solver_opts;
+
+/* Details of the last solve on a context (filled by gmaf_solve_joint and
+ * gmaf_picard_step). */
+typedef struct {
+    int32_t iterations;        /* PCG iterations (inner iterations summed in mixed mode) */
+    int32_t outer_iterations;  /* iterative-refinement sweeps (mixed), 1 in FP64          */
+    int32_t restarts;          /* restarts after a true-residual check failed            */
+    int32_t status;
+    double rel_residual;       /* recurrence relative residual at exit (FP64 mode)       */
+    double true_rel_residual;  /* ||S - A p|| / ||S|| at exit, in FP64                   */
+} gmaf_solve_info;
+
+typedef struct gmaf_ctx gmaf_ctx;
+
+/* Create a context on the current CUDA device.  hbm_budget_bytes caps the
+ * workspace the library may allocate (0 = no cap).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  *out receives the context. */
+int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Synchronise the context's stream and free the context and its workspace. */
+int gmaf_destroy(gmaf_ctx *ctx);
+
+/* Change the stream subsequent calls are issued on. */
+int gmaf_set_stream(gmaf_ctx *ctx, void *cuda_stream);
+
+/* Bytes of device workspace currently held by the context. */
+int gmaf_workspace_bytes(const gmaf_ctx *ctx, size_t *bytes_out);
+
+/* Details of the last solve. */
+int gmaf_last_solve_info(const gmaf_ctx *ctx, gmaf_solve_info *info_out);
+
+/* FVM assembly of the Reynolds equation (Sec. 2.1, Eq. 2.1-2.7; Sec. 2.4-I).
+ * conds: host array of n_cond states.  D, aE, aN, S: device arrays of
+ * n_cond * n_z * n_theta doubles, written.  Row P of condition k reads
+ *   D p_P - aE[P] p_E - aE[W] p_W - aN[P] p_N - aN[S] p_S = S[P]
+ * (aE couples i to i+1 with periodic wrap, aN couples j to j+1 and is 0 in
+ * the last row; the half-cell Dirichlet terms are inside D and S).
+ * Returns GMAF_CONTACT (arrays still written) when some h <= 0.  Synchronises
+ * the stream only to read the contact flag. */
+int gmaf_assemble(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *phys,
+                  const gmaf_texture *tex, const gmaf_state *conds, int32_t n_cond,
+                  double *D, double *aE, double *aN, double *S);
+
+/* Joint PCG on the block-diagonal system of n_cond conditions (Table 1,
+ * Eq. 3.7-3.9) with one set of scalars for the whole joint system.
+ * D, aE, aN, S: device arrays as written by gmaf_assemble.  p: device array
+ * (n_cond * n), initial guess unless opts->zero_init, overwritten with the
+ * solution.  iters_out, rel_res_out: host outputs (may be NULL); rel_res_out
+ * receives the true relative residual ||S - A p|| / ||S|| in FP64.
+ * Synchronises the stream.  GMAF_NOT_CONVERGED leaves the last iterate in p. */
+int gmaf_solve_joint(gmaf_ctx *ctx, const gmaf_grid *grid, int32_t n_cond,
+                     const double *D, const double *aE, const double *aN, const double *S,
+                     double *p, const gmaf_solver_opts *opts, int32_t *iters_out,
+                     double *rel_res_out);
+
+/* Loads from the pressure fields (Sec. 2.4-III): per condition, force and
+ * moment (Fx, Fy, Fz, Mx, My, Mz) from normal pressure and from viscous shear,
+ * integrated on the elements bounded by cell centres and the two boundary
+ * lines, moments about the bore axis at z = 0.  conds: host array (for the
+ * film thickness in the shear stress).  p: device array (n_cond * n).
+ * loads: device array of n_cond * 12 doubles, written as
+ * [k][0..5] pressure part, [k][6..11] shear part.  Asynchronous. */
+int gmaf_integrate_loads(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *phys,
+                         const gmaf_texture *tex, const gmaf_state *conds, int32_t n_cond,
+                         const double *p, double *loads);
+
+/* One general (double-Jacobian) Picard iteration (Eq. 2.12-2.19), all on the
+ * device: fan-out into the 9 conditions (base, e_j + d_e, edot_j + d_edot),
+ * assembly, joint solve, loads, the 6 x 8 Jacobian of the total (pressure +
+ * shear) loads by forward differences (Eq. 2.13-2.14), the generalized force
+ *   G = (Fx - My/L, Fy + Mx/L, My/L, -Mx/L) + F_ext
+ * and the update of (e, edot) from (J_edot + dt J_e) delta = -G - J_e (e_prev
+ * + dt edot - e), edot += delta, e = e_prev + dt edot.
+ * All arguments are host memory.  state is updated in place only when the
+ * solve converged.  loads_out[12]: loads of the base condition; J_out[48]:
+ * row-major 6 x 8 Jacobian (columns e1..e4, edot1..edot4); G_out[4]: G before
+ * the update.  Synchronises the stream. */
+int gmaf_picard_step(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *phys,
+                     const gmaf_texture *tex, gmaf_state *state, const double e_prev[4],
+                     double dt, const double F_ext[4], double d_e, double d_edot,
+                     const gmaf_solver_opts *opts, double loads_out[12], double J_out[48],
+                     double G_out[4], int32_t *iters_out);
+
+/* Static description of a status code. */
+const char *gmaf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMAF_H */

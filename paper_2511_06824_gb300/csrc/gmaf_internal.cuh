@@ -1,0 +1,149 @@
+// Internal declarations of the GB300 piston-gap library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "gmaf.h"
+
+namespace gmaf {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxCond = 64;       // conditions in one joint system
+constexpr int kThreads = 256;      // threads per block of the stencil kernels
+
+// ---------------------------------------------------------------- geometry
+
+// Hexagonal lattice of flat-bottom circular dimples (h_Text of Eq. 2.3).
+struct Lattice {
+    int on;
+    double r, depth, oth, oz;
+    double ath, az;   // column pitch around the piston, row pitch along z
+};
+
+struct Geom {
+    int nth, nz;
+    double Rk, L, c, mu, v, pch, pcase;
+    double dth, dx, dz, invL;
+    Lattice lt;
+};
+
+Lattice make_lattice(const gmaf_texture *tex, double Rk);
+Geom make_geom(const gmaf_grid *g, const gmaf_physics *ph, const gmaf_texture *tex);
+
+// ---------------------------------------------------------------- solver state
+
+// Scalars of one joint PCG run, resident on the device.
+struct Scalars {
+    double alpha, beta, d;
+    double normS, rel, true_rel;
+    double scale;           // mixed precision: FP32 matrix = scale * A
+    double rnorm;           // mixed precision: norm of the FP64 outer residual
+    int iter, first, done, converged, status, pending, guard, zero_rhs;
+    int max_iter;
+    unsigned int ticket[6];
+};
+
+enum Ticket { kTicketA = 0, kTicketB = 1, kTicketInit = 2, kTicketResid = 3, kTicketMisc = 4 };
+
+template <typename T>
+struct PcgDesc {
+    int nth, nz, K, tiles_x, tiles_y, precond, zero_init, use_cond;
+    long long n, ntiles;
+    const T *D, *invD, *aE, *aN;   // coefficient slots, [slot][n]
+    const int *cslot;              // coefficient slot of each condition, [K]
+    const T *b;                    // right-hand side, [K][n]
+    T *p, *z, *v;
+    T *u[2], *r[2];
+    T omega, c1;                   // c1 = omega (2 - omega)
+    double eps;
+    int max_iter;
+    cudaGraphConditionalHandle cond;
+    Scalars *sc;
+    double *partials;              // [2][grid]
+};
+
+// FP64 residual r = S - A p over all conditions, with ||r||^2 and ||S||^2.
+struct ResidDesc {
+    int nth, nz, K;
+    long long n;
+    const double *D, *aE, *aN;
+    const int *cslot;
+    const double *S, *p;
+    double *r;                     // written (may be null)
+    Scalars *sc;
+    double *partials;
+};
+
+// ---------------------------------------------------------------- context
+
+enum BufId {
+    B_TRIG, B_FLAGS, B_CONDS, B_CSLOT, B_SCAL, B_PART, B_DESC, B_LOADPART, B_LOADS, B_RESULT,
+    // FP64 coefficient slots / fields owned by the Picard step
+    B_PD, B_PAE, B_PAN, B_PS, B_PP,
+    // FP64 PCG workspace
+    B_INVD, B_R0, B_R1, B_U0, B_U1, B_Z, B_V,
+    // mixed-precision workspace
+    B_D32, B_INVD32, B_AE32, B_AN32, B_B32, B_X32, B_R032, B_R132, B_U032, B_U132, B_Z32, B_V32,
+    B_R64,
+    B_COUNT
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle handle = 0;
+    int grid_a = 0, grid_b = 0, grid_s = 0;
+    const void *desc = nullptr;
+};
+
+}  // namespace gmaf
+
+struct gmaf_ctx {
+    int device;
+    cudaStream_t stream;
+    size_t budget;
+    size_t held;
+    void *buf[gmaf::B_COUNT];
+    size_t bytes[gmaf::B_COUNT];
+    void *pinned;                  // pinned host staging, kPinnedBytes
+    gmaf_solve_info info;
+    gmaf::GraphCache graph64, graph32;
+    int num_sms;
+    int no_graph;                  // loop control by host chunks instead of a graph
+};
+
+namespace gmaf {
+
+constexpr size_t kPinnedBytes = 64 * 1024;
+
+int ensure(gmaf_ctx *ctx, int id, size_t bytes);
+int cuda_status(cudaError_t e);
+bool geom_valid(const gmaf_grid *g, const gmaf_physics *ph, const gmaf_texture *tex);
+bool opts_valid(const gmaf_solver_opts *o);
+
+// geometry / assembly / loads / Picard kernels (gmaf_assemble.cu)
+int launch_trig(const Geom &g, double *trig, cudaStream_t s);
+int launch_fanout(const double *base, double d_e, double d_edot, double *conds, int *cslot_write,
+                  cudaStream_t s);
+int launch_assemble(const Geom &g, int ncond, const double *conds, const int *coef_slot,
+                    double *D, double *aE, double *aN, double *S, const double *trig, int *flags,
+                    int nslots, cudaStream_t s);
+int launch_loads(const Geom &g, int ncond, const double *conds, const double *p,
+                 const double *trig, double *partials, unsigned int *tickets, double *loads,
+                 int *flags, int num_sms, cudaStream_t s);
+struct PicardIn {
+    double base[8], e_prev[4], F_ext[4];
+};
+constexpr int kResultDoubles = 73;
+int launch_picard_update(const double *loads, const PicardIn &in, double dt, double d_e,
+                         double d_edot, double L, double *result, cudaStream_t s);
+size_t loads_partials_bytes(int ncond, int num_sms);
+
+// joint PCG (gmaf_pcg.cu).  Coefficient slots in device memory, FP64.
+int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const int *cslot_host,
+                       const double *D, const double *aE, const double *aN, const double *S,
+                       double *p, const gmaf_solver_opts *opts, gmaf_solve_info *info);
+
+}  // namespace gmaf

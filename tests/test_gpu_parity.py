@@ -1,0 +1,273 @@
+"""GPU vs oracle parity through the C ABI (needs a GB300 and the built library).
+
+Tolerances (FP64 mode): coefficients rtol 1e-11 (the film thickness is a
+difference of two ~R_k numbers, so ~3e-14 relative; cubed and divided it stays
+below 1e-12; cos/sin may differ by an ulp between libm and CUDA), sources rtol
+1e-9 against the interior scale (h_n - h_s is a further cancellation of
+~1e-3), pressure relative L2 1e-9 and loads 1e-7 normalised by
+max(|F_c|, 1e-3 ||F||).  Mixed mode: pressure 1e-6, loads 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_06824_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PHYS = inputs.phys_vector()
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_06824_gb300 import build, gmaf
+    build.build()
+    gmaf.load()
+    return gmaf
+
+
+@pytest.fixture(scope="module")
+def ctx(g):
+    c = g.Context()
+    yield c.handle
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).cuda()
+
+
+def zeros(n):
+    return torch.zeros(n, dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def tex_dimples(seed=5):
+    return inputs.dimple_texture(np.random.default_rng(seed))
+
+
+def states(K, seed=1):
+    rng = np.random.default_rng(seed)
+    return [inputs.random_state(rng) for _ in range(K)]
+
+
+def load_err(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    out = 0.0
+    for part in (slice(0, 6), slice(6, 12)):
+        x, y = a[..., part], b[..., part]
+        nrm = np.linalg.norm(y, axis=-1, keepdims=True)
+        scale = np.maximum(np.abs(y), 1e-3 * nrm)
+        out = max(out, float(np.max(np.abs(x - y) / scale)))
+    return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def gpu_assemble(g, ctx, nth, nz, tex, conds, allow_contact=False):
+    K = len(conds)
+    n = K * nth * nz
+    D, aE, aN, S = zeros(n), zeros(n), zeros(n), zeros(n)
+    st = g.gmaf_assemble(ctx, nth, nz, PHYS, tex, conds, D, aE, aN, S, allow_contact=allow_contact)
+    sh = (K, nz, nth)
+    return st, host(D).reshape(sh), host(aE).reshape(sh), host(aN).reshape(sh), host(S).reshape(sh)
+
+
+# ----------------------------------------------------------------------------- assembly
+
+
+@pytest.mark.parametrize("nth,nz,K,textured", [(64, 32, 1, False), (100, 37, 3, True),
+                                               (3, 2, 2, True), (512, 256, 2, True),
+                                               (129, 17, 9, False)])
+def test_assembly_matches_oracle(g, ctx, nth, nz, K, textured):
+    tex = tex_dimples() if textured else inputs.smooth_texture()
+    conds = states(K, seed=nth)
+    st, D, aE, aN, S = gpu_assemble(g, ctx, nth, nz, tex, conds)
+    so, Do, aEo, aNo, So = oracle.assemble_joint(nth, nz, PHYS, tex, conds)
+    assert st == 0 and so == 0
+    np.testing.assert_allclose(aE, aEo, rtol=1e-11)
+    np.testing.assert_allclose(aN, aNo, rtol=1e-11, atol=0)
+    np.testing.assert_allclose(D, Do, rtol=1e-11)
+    scale = np.abs(So[:, 1:-1]).max() if nz > 2 else np.abs(So).max()
+    np.testing.assert_allclose(S, So, rtol=1e-9, atol=1e-9 * scale)
+
+
+def test_texture_decisions_are_identical(g, ctx):
+    """Dimple membership is an integer decision: the conductance jumps by (1 + depth/h)^3,
+    so any disagreement would show as an O(1) relative error."""
+    nth, nz = 2048, 64
+    tex = tex_dimples(seed=9)
+    conds = states(1, seed=2)
+    _, _, aE, aN, _ = gpu_assemble(g, ctx, nth, nz, tex, conds)
+    _, _, aEo, aNo, _ = oracle.assemble_joint(nth, nz, PHYS, tex, conds)
+    assert np.max(np.abs(aE / aEo - 1)) < 1e-11
+    assert np.max(np.abs(aN[:, :-1] / aNo[:, :-1] - 1)) < 1e-11
+
+
+def test_contact_is_reported(g, ctx):
+    c = inputs.CLEARANCE
+    st, *_ = gpu_assemble(g, ctx, 16, 8, inputs.smooth_texture(),
+                          [np.array([1.2 * c, 0, 1.2 * c, 0, 0, 0, 0, 0])], allow_contact=True)
+    assert st == g.GMAF_CONTACT
+
+
+# ----------------------------------------------------------------------------- solver
+
+
+def solve_both(g, ctx, nth, nz, tex, conds, precond=1, omega=1.2, eps=1e-10, precision=0):
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex, conds)
+    K = len(conds)
+    n = K * nth * nz
+    p = zeros(n)
+    opts = g.solver_opts(precond=precond, omega=omega, eps=eps, precision=precision)
+    st, it, rel = g.gmaf_solve_joint(ctx, nth, nz, K, dev(D), dev(aE), dev(aN), dev(S), p, opts)
+    sto, po, ito, relo, trelo = oracle.solve_joint(nth, nz, D, aE, aN, S, precond=precond,
+                                                   omega=omega, eps=eps)
+    assert sto == 0
+    return host(p).reshape(K, nz, nth), it, rel, po, ito, (D, aE, aN, S)
+
+
+@pytest.mark.parametrize("nth,nz,K,textured,precond", [
+    (64, 32, 1, False, 1),        # single condition, smooth
+    (130, 45, 9, True, 1),        # joint batch, ragged tiles, textured
+    (96, 40, 4, False, 0),        # Jacobi
+    (3, 2, 1, False, 1),          # smallest grid
+    (257, 9, 2, True, 1),         # one tile row, ragged in theta
+])
+def test_fp64_solve_matches_oracle(g, ctx, nth, nz, K, textured, precond):
+    tex = tex_dimples() if textured else inputs.smooth_texture()
+    conds = states(K, seed=nth + nz)
+    p, it, rel, po, ito, _ = solve_both(g, ctx, nth, nz, tex, conds, precond=precond)
+    assert rel <= 1e-9
+    assert abs(it - ito) <= 2, (it, ito)
+    assert rel_l2(p, po) <= 1e-9
+
+
+def test_fp64_iterates_track_the_oracle_tightly(g, ctx):
+    """Same algorithm, same ordering of steps: iteration counts agree and the
+    solutions agree far below the tolerance at a tight criterion."""
+    conds = states(9, seed=4)
+    p, it, rel, po, ito, _ = solve_both(g, ctx, 200, 60, tex_dimples(), conds, eps=1e-12)
+    assert abs(it - ito) <= 1
+    assert rel_l2(p, po) <= 1e-11
+
+
+@pytest.mark.parametrize("nth,nz,K", [(64, 32, 1), (130, 45, 9)])
+def test_mixed_precision_solve_matches_fp64_oracle(g, ctx, nth, nz, K):
+    conds = states(K, seed=7)
+    p, it, rel, po, ito, arrs = solve_both(g, ctx, nth, nz, tex_dimples(), conds, precision=1)
+    assert rel <= 1e-10
+    assert rel_l2(p, po) <= 1e-6
+    info = g.gmaf_last_solve_info(ctx)
+    assert info["outer_iterations"] >= 2
+
+
+def test_warm_start_zero_rhs_budget_and_invalid(g, ctx):
+    nth, nz = 64, 32
+    conds = states(2, seed=3)
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, inputs.smooth_texture(), conds)
+    n = 2 * nth * nz
+    Dd, aEd, aNd, Sd = dev(D), dev(aE), dev(aN), dev(S)
+    p = zeros(n)
+    opts = g.solver_opts(eps=1e-12)
+    st, it, rel = g.gmaf_solve_joint(ctx, nth, nz, 2, Dd, aEd, aNd, Sd, p, opts)
+    assert st == 0 and it > 10
+    before = p.clone()
+    st, it2, rel2 = g.gmaf_solve_joint(ctx, nth, nz, 2, Dd, aEd, aNd, Sd, p,
+                                       g.solver_opts(eps=1e-10, zero_init=0))
+    assert st == 0 and it2 == 0 and torch.equal(before, p)
+    p.fill_(123.0)
+    st, it3, rel3 = g.gmaf_solve_joint(ctx, nth, nz, 2, Dd, aEd, aNd, zeros(n), p,
+                                       g.solver_opts(zero_init=0))
+    assert st == 0 and it3 == 0 and not torch.any(p)
+    st, it4, _ = g.gmaf_solve_joint(ctx, nth, nz, 2, Dd, aEd, aNd, Sd, p,
+                                    g.solver_opts(eps=1e-12, max_iter=3), allow_not_converged=True)
+    assert st == g.GMAF_NOT_CONVERGED and it4 == 3
+    for bad in (g.solver_opts(omega=2.0), g.solver_opts(eps=0.0), g.solver_opts(precond=3),
+                g.solver_opts(max_iter=-1)):
+        with pytest.raises(g.GmafError) as ei:
+            g.gmaf_solve_joint(ctx, nth, nz, 2, Dd, aEd, aNd, Sd, p, bad)
+        assert ei.value.status == g.GMAF_INVALID_ARG
+    with pytest.raises(g.GmafError):
+        g.gmaf_solve_joint(ctx, 2, nz, 2, Dd, aEd, aNd, Sd, p)
+
+
+def test_solve_is_deterministic_and_graph_matches_host_loop(g, ctx, monkeypatch):
+    conds = states(9, seed=11)
+    nth, nz = 150, 50
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
+    args = [dev(D), dev(aE), dev(aN), dev(S)]
+    n = 9 * nth * nz
+    outs = []
+    for _ in range(2):
+        p = zeros(n)
+        g.gmaf_solve_joint(ctx, nth, nz, 9, *args, p)
+        outs.append(host(p))
+    assert np.array_equal(outs[0], outs[1])
+    monkeypatch.setenv("GMAF_NO_GRAPH", "1")
+    c2 = g.Context()
+    p = zeros(n)
+    g.gmaf_solve_joint(c2.handle, nth, nz, 9, *args, p)
+    c2.close()
+    assert np.array_equal(host(p), outs[0])
+
+
+def test_hbm_budget_is_enforced(g):
+    c = g.Context(hbm_budget_bytes=1 << 20)
+    n = 9 * 256 * 128
+    with pytest.raises(g.GmafError) as ei:
+        g.gmaf_picard_step(c.handle, 256, 128, PHYS, None, np.zeros(8), np.zeros(4), 1e-4,
+                           np.zeros(4), 2e-8, 1e-6)
+    assert ei.value.status == g.GMAF_OUT_OF_MEMORY
+    c.close()
+
+
+# ----------------------------------------------------------------------------- loads
+
+
+@pytest.mark.parametrize("nth,nz,K,textured", [(64, 32, 1, False), (130, 45, 9, True),
+                                               (3, 2, 2, False)])
+def test_loads_match_oracle(g, ctx, nth, nz, K, textured):
+    tex = tex_dimples() if textured else inputs.smooth_texture()
+    conds = states(K, seed=21)
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex, conds)
+    sto, po, *_ = oracle.solve_joint(nth, nz, D, aE, aN, S, eps=1e-12)
+    loads = zeros(12 * K)
+    g.gmaf_integrate_loads(ctx, nth, nz, PHYS, tex, conds, dev(po), loads)
+    got = host(loads).reshape(K, 12)
+    want = np.stack([oracle.loads(nth, nz, PHYS, tex, c, po[k])[1] for k, c in enumerate(conds)])
+    assert load_err(got, want) <= 1e-11
+
+
+# ----------------------------------------------------------------------------- whole Picard step
+
+
+@pytest.mark.parametrize("nth,nz,textured,precision", [(64, 32, False, 0), (96, 48, True, 0),
+                                                       (96, 48, True, 1)])
+def test_picard_step_matches_oracle(g, ctx, nth, nz, textured, precision):
+    tex = tex_dimples() if textured else inputs.smooth_texture()
+    st0 = states(1, seed=31)[0]
+    e_prev = st0[:4] - 2e-8
+    Fext = np.array([25.0, -10.0, 4.0, 3.0])
+    dt = 2.78e-4
+    eps = 1e-12
+    r = g.gmaf_picard_step(ctx, nth, nz, PHYS, tex, st0, e_prev, dt, Fext, 2e-8, 1e-6,
+                           g.solver_opts(eps=eps, precision=precision))
+    o = oracle.picard_step(nth, nz, PHYS, tex, st0, e_prev, dt, Fext, 2e-8, 1e-6, eps=eps)
+    assert r["status"] == 0 and o["status"] == 0
+    tol_l = 1e-7 if precision == 0 else 1e-5
+    assert load_err(r["loads"], o["loads"]) <= tol_l
+    Jg, Jo = r["J"], o["J"]
+    colscale = np.abs(Jo).max(axis=0, keepdims=True)
+    assert np.max(np.abs(Jg - Jo) / colscale) <= (1e-5 if precision == 0 else 1e-3)
+    np.testing.assert_allclose(r["G"], o["G"], rtol=1e-6, atol=1e-6 * np.abs(o["G"]).max())
+    ds_g, ds_o = r["state"] - st0, o["state"] - st0
+    assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o) + 1e-20
