@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the GMAF hot path on GB300.
+
+One step = one general Picard iteration of the joint 9-condition batch (base
+state + 4 eccentricity + 4 rate perturbations) on the textured piston gap,
+2048 x 1024 cells per condition (18.9 M joint DOF): condition fan-out, FVM
+assembly, the joint ASSOR-PCG solve under the synchronized criterion, load
+integration, the 6 x 8 Jacobian and the 4 x 4 update, all on the GPU through
+the C ABI (gmaf_picard_step).
+
+Metric: joint ASSOR-PCG DOF.iter/s (joint DOF x PCG iterations per second of
+whole steps), with Picard steps/s beside it.  The headline runs the
+mixed-precision mode (FP32 stencil/ASSOR/updates, FP64-accurate dot products,
+FP64 residual and iterative refinement); an FP64-mode measurement of the same
+workload is reported under "fp64".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 C restatement under
+oracle/) on a bounded sample of the same workload on the host cores.
+With --gpus N > 1 (torchrun), each rank runs an independent replica (the path
+has no exchange step); value = the units of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "textured-2048x1024-k9"
+METRIC = "joint ASSOR-PCG DOF*iter/s"
+UNIT = "DOF*iter/s"
+DT = (60.0 / 600.0) / 360.0        # one shaft-angle degree at 600 rpm
+L2_BYTES = 135528448
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def alg_bytes_per_dof(precision: str, n_cond: int = 9, n_slots: int = 5):
+    """Algorithmic bytes per joint DOF per launch of each PCG phase.
+
+    phase A reads z, u', p and writes u, v, p; phase B reads r, v and writes r, z;
+    each phase reads three coefficient arrays (D, a_E, a_N in A; 1/D, a_E, a_N in B),
+    stored once per coefficient slot: 5 slots serve the 9 conditions because the
+    rate-perturbed conditions share the matrix of the base condition."""
+    w = 4 if precision == "mixed" else 8
+    coef = 3 * w * n_slots / n_cond
+    return {"phase_a": 6 * w + coef, "phase_b": 4 * w + coef}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("gmaf_pcg.cu", "gmaf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2511_06824_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, precision: str, kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pcg_phases_dram.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 6 and f[0] == "traffic" and f[1] == want and f[2] == workload and \
+                f[3] == precision and f[4] == kernel:
+            return float(f[5])
+    return None
+
+
+# ----------------------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2511_06824_gb300 import build as gbuild
+    from paper_2511_06824_gb300 import gmaf, inputs
+    gbuild.build()
+    gmaf.load()
+
+    w = inputs.make(args.workload, args.seed + rank)
+    prec = 1 if args.precision == "mixed" else 0
+    e_prev = w.state[:4].copy()
+    F_ext = np.array([40.0, -20.0, 8.0, -4.0])
+    ctx = gmaf.Context()
+    stream = torch.cuda.current_stream()
+
+    def step(opts):
+        return gmaf.gmaf_picard_step(ctx.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state, e_prev,
+                                     DT, F_ext, w.d_e, w.d_edot, opts)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(opts, K, W, sample_clocks):
+        for _ in range(W):
+            step(opts)
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        its, outer = [], []
+        for _ in range(K):
+            r = step(opts)
+            its.append(r["iters"])
+            outer.append(gmaf.gmaf_last_solve_info(ctx.handle)["outer_iterations"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, its, outer, clocks
+
+    opts = gmaf.solver_opts(precond=1, omega=w.omega, eps=w.eps, precision=prec)
+    K, W = args.steps, max(3, args.warmup)
+    ms, its, outer, clocks = timed(opts, K, W, True)
+    total_dof_iter = float(sum(its)) * w.dof * world
+    value = total_dof_iter / (ms / 1e3)
+    picard_rate = K * world / (ms / 1e3)
+
+    # launches of our kernels in one step: fan-out, trig, 2 assembly, loads, update,
+    # and per solve: conversion/inverse, and per PCG run reset, init_r, init B,
+    # 2 per iteration, finalize, plus the FP64 residual and the mixed-mode glue
+    def launches_per_step(iters, outer_it):
+        fixed = 6
+        if prec == 1:
+            return fixed + 1 + outer_it * 6 + 1 + 2 * iters
+        return fixed + 1 + 4 + 1 + 2 * iters
+
+    gpu_launches = int(sum(launches_per_step(i, o) for i, o in zip(its, outer)))
+
+    # end to end: the public call with host buffers (pinned), copies inside the timed region
+    pin_in = torch.empty(16, dtype=torch.float64).pin_memory()
+    pin_in[:8] = torch.from_numpy(w.state)
+    pin_in[8:12] = torch.from_numpy(e_prev)
+    pin_in[12:16] = torch.from_numpy(F_ext)
+    host_in = pin_in.numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        gmaf.gmaf_picard_step(ctx.handle, w.n_theta, w.n_z, w.phys, w.tex, host_in[:8],
+                              host_in[8:12], DT, host_in[12:16], w.d_e, w.d_edot, opts)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    structs = sum(ctypes.sizeof(c) for c in (gmaf.gmaf_grid, gmaf.gmaf_physics,
+                                              gmaf.gmaf_texture, gmaf.gmaf_solver_opts))
+    h2d = 16 * 8 + 3 * 8 + structs
+    d2h = (12 + 48 + 4 + 8) * 8 + 4
+
+    # per-phase kernel durations (events around each launch; same kernels, host-chunked loop)
+    gmaf.gmaf_set_phase_timing(ctx.handle, True)
+    step(opts)
+    ph = gmaf.gmaf_phase_timing(ctx.handle)
+    gmaf.gmaf_set_phase_timing(ctx.handle, False)
+    hbm, peak_kind = peaks()
+    bpd = alg_bytes_per_dof(args.precision)
+    phases = {}
+    for k in ("phase_a", "phase_b"):
+        tot, cnt = ph[k]
+        avg = tot / max(cnt, 1)
+        gbs = bpd[k] * w.dof / (avg / 1e3) / 1e9
+        phases[k] = {"launches": cnt, "avg_ms": avg, "alg_bytes_per_dof": bpd[k],
+                     "achieved_gbs": gbs, "frac": gbs / hbm, "share": tot}
+    share_tot = sum(v["share"] for v in phases.values())
+    for v in phases.values():
+        v["share"] = v["share"] / share_tot if share_tot else None
+    dom = max(phases, key=lambda k: phases[k]["share"] or 0)
+    d = phases[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["achieved_gbs"], 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(d["frac"], 4),
+                "traffic": ncu_traffic(args.workload, args.precision, dom),
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json copy bandwidth)",
+                "alg_bytes_per_launch": bpd[dom] * w.dof}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_theta": w.n_theta, "n_z": w.n_z,
+                   "n_cond": w.n_cond, "joint_dof": w.dof, "precond": "ASSOR-II",
+                   "omega": w.omega, "eps": w.eps, "precision": args.precision,
+                   "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2 (working set > {L2_BYTES // 2**20} MiB)"},
+        "picard_steps_per_s": picard_rate,
+        "pcg_iterations_per_step": float(np.mean(its)),
+        "outer_refinements_per_step": float(np.mean(outer)),
+        "e2e": {"value": float(sum(its)) * w.dof * world / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "picard_steps_per_s": K * world / t_e2e},
+        "gpu_launches": gpu_launches,
+        "roofline": roofline,
+        "phases": phases,
+        "clocks": clocks,
+    }
+
+    if not args.no_fp64:
+        o64 = gmaf.solver_opts(precond=1, omega=w.omega, eps=w.eps, precision=0)
+        K64 = 2
+        ms64, its64, _, _ = timed(o64, K64, 1, False)
+        gmaf.gmaf_set_phase_timing(ctx.handle, True)
+        step(o64)
+        ph64 = gmaf.gmaf_phase_timing(ctx.handle)
+        gmaf.gmaf_set_phase_timing(ctx.handle, False)
+        b64 = alg_bytes_per_dof("fp64")
+        p64 = {}
+        for k in ("phase_a", "phase_b"):
+            tot, cnt = ph64[k]
+            avg = tot / max(cnt, 1)
+            gbs = b64[k] * w.dof / (avg / 1e3) / 1e9
+            p64[k] = {"avg_ms": avg, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm}
+        out["fp64"] = {"ms_per_step": ms64 / K64,
+                       "value": float(sum(its64)) * w.dof * world / (ms64 / 1e3),
+                       "picard_steps_per_s": K64 * world / (ms64 / 1e3),
+                       "pcg_iterations_per_step": float(np.mean(its64)), "phases": p64,
+                       "note": "FP64 mode is bound by GB300's FP64 pipe, not by HBM"}
+    ctx.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, budget_s=25.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+
+
+def oracle_sample(w, iters: int):
+    """Time the oracle's joint PCG for `iters` iterations on the workload's assembled
+    system, minus the same call with 0 iterations (set-up and the final residual)."""
+    import oracle
+    K = w.n_cond
+    base = w.state
+    conds = [base.copy() for _ in range(K)]
+    for j in range(4):
+        conds[1 + j][j] += w.d_e
+        conds[5 + j][4 + j] += w.d_edot
+    t0 = time.perf_counter()
+    st, D, aE, aN, S = oracle.assemble_joint(w.n_theta, w.n_z, w.phys, w.tex, conds)
+    t_asm = time.perf_counter() - t0
+
+    def run(m):
+        t = time.perf_counter()
+        oracle.solve_joint(w.n_theta, w.n_z, D, aE, aN, S, omega=w.omega, eps=w.eps, max_iter=m)
+        return time.perf_counter() - t
+
+    t_zero = run(0)
+    t_it = run(iters)
+    per_iter = max(t_it - t_zero, 1e-9) / iters
+    return per_iter, t_asm, t_zero
+
+
+def cpu_baseline(w, budget_s=25.0):
+    per_iter, t_asm, t_zero = oracle_sample(w, 4)
+    return {"value": w.dof / per_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FP64 joint ASSOR-PCG on the full {w.name} system: 4 iterations "
+                       f"timed minus a 0-iteration call (set-up {t_zero:.1f} s); assembly of the "
+                       f"9 conditions took {t_asm:.1f} s"),
+            "s_per_iteration": per_iter}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2511_06824_gb300 import inputs
+    import oracle
+    oracle.build()
+    w = inputs.make(args.workload, args.seed)
+    K, W = args.steps, max(args.warmup, 0)
+    # each step: the oracle's joint PCG for a bounded number of iterations (plus its
+    # fixed set-up), sized so that the whole run stays within a few minutes
+    per_iter, t_asm, t_zero = oracle_sample(w, 2)
+    budget = 150.0 / max(K + W, 1)
+    m = int(max(1, min(50, (budget - t_zero) / per_iter)))
+    conds = [w.state.copy() for _ in range(w.n_cond)]
+    for j in range(4):
+        conds[1 + j][j] += w.d_e
+        conds[5 + j][4 + j] += w.d_edot
+    st, D, aE, aN, S = oracle.assemble_joint(w.n_theta, w.n_z, w.phys, w.tex, conds)
+    for _ in range(W):
+        oracle.solve_joint(w.n_theta, w.n_z, D, aE, aN, S, omega=w.omega, eps=w.eps, max_iter=m)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        oracle.solve_joint(w.n_theta, w.n_z, D, aE, aN, S, omega=w.omega, eps=w.eps, max_iter=m)
+    dt = time.perf_counter() - t0
+    value = K * m * w.dof / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "n_theta": w.n_theta, "n_z": w.n_z,
+                      "n_cond": w.n_cond, "joint_dof": w.dof, "precond": "ASSOR-II",
+                      "omega": w.omega, "eps": w.eps},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"each step: oracle joint PCG, {m} iterations incl. "
+                                      f"set-up, on the full {w.name} system"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

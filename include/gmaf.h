@@ -175,6 +175,17 @@ int gmaf_picard_step(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *p
                      const gmaf_solver_opts *opts, double loads_out[12], double J_out[48],
                      double G_out[4], int32_t *iters_out);
 
+/* Per-phase kernel timing (tracing).  When enabled (on != 0), the PCG loop of
+ * later solves is driven in host chunks instead of the graph WHILE node, with a
+ * CUDA event pair around every phase launch on the context's stream; results
+ * are bitwise the same.  gmaf_phase_timing returns, per kernel kind
+ * [0] phase A (u update + stencil), [1] phase B (residual update + ASSOR-II),
+ * [2] initial preconditioner pass, [3] FP64 residual, the summed event time in
+ * milliseconds and the number of launches since timing was enabled.  Enabling
+ * resets the sums. */
+int gmaf_set_phase_timing(gmaf_ctx *ctx, int on);
+int gmaf_phase_timing(const gmaf_ctx *ctx, double ms_out[4], int64_t launches_out[4]);
+
 /* Static description of a status code. */
 const char *gmaf_status_string(int status);
 

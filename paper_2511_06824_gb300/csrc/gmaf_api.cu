@@ -144,6 +144,8 @@ int gmaf_destroy(gmaf_ctx *c)
     for (int i = 0; i < B_COUNT; ++i)
         if (c->buf[i]) cudaFree(c->buf[i]);
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->ev_ready)
+        for (auto &ev : c->ev) cudaEventDestroy(ev);
     delete c;
     return e == cudaSuccess ? GMAF_OK : GMAF_CUDA_ERROR;
 }
@@ -154,6 +156,34 @@ int gmaf_set_stream(gmaf_ctx *c, void *cuda_stream)
     cudaError_t e = cudaStreamSynchronize(c->stream);
     c->stream = (cudaStream_t)cuda_stream;
     return cuda_status(e);
+}
+
+int gmaf_set_phase_timing(gmaf_ctx *c, int on)
+{
+    if (!c) return GMAF_INVALID_ARG;
+    if (on && !c->ev_ready) {
+        for (auto &ev : c->ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        c->ev_ready = 1;
+    }
+    c->phase_timing = on ? 1 : 0;
+    for (int q = 0; q < 4; ++q) {
+        c->phase_ms[q] = 0.0;
+        c->phase_count[q] = 0;
+    }
+    return GMAF_OK;
+}
+
+int gmaf_phase_timing(const gmaf_ctx *c, double ms_out[4], int64_t launches_out[4])
+{
+    if (!c || !ms_out || !launches_out) return GMAF_INVALID_ARG;
+    for (int q = 0; q < 4; ++q) {
+        ms_out[q] = c->phase_ms[q];
+        launches_out[q] = c->phase_count[q];
+    }
+    return GMAF_OK;
 }
 
 int gmaf_workspace_bytes(const gmaf_ctx *c, size_t *bytes_out)

@@ -112,6 +112,11 @@ struct gmaf_ctx {
     gmaf::GraphCache graph64, graph32;
     int num_sms;
     int no_graph;                  // loop control by host chunks instead of a graph
+    int phase_timing;              // events around each phase launch (host chunks)
+    double phase_ms[4];
+    long long phase_count[4];
+    cudaEvent_t ev[2 * 2 * 16 + 2];
+    int ev_ready;
 };
 
 namespace gmaf {

@@ -697,10 +697,16 @@ static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
 }
 
 // Upload the descriptor, building the loop graph first when needed.
+// The loop runs as a graph WHILE node unless the host drives it in chunks
+// (GMAF_NO_GRAPH, or per-phase event timing).  Only kernels launched by that
+// graph may write its condition, so the descriptor enables the condition
+// writes exactly when the graph is used.
+static bool use_graph(const gmaf_ctx *ctx) { return !ctx->no_graph && !ctx->phase_timing; }
+
 template <typename T>
 static int prepare(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc)
 {
-    if (ctx->no_graph) {
+    if (!use_graph(ctx)) {
         run.h.use_cond = 0;
     } else {
         if (!graph_matches(gc, run.grid_a, run.grid_b, run.grid_s, run.d_desc))
@@ -713,6 +719,36 @@ static int prepare(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc)
     return GMAF_OK;
 }
 
+// Event pair around a launch when phase timing is on.
+struct PhaseClock {
+    gmaf_ctx *ctx;
+    int used = 0;
+    int kinds[33];
+    bool on() const { return ctx->phase_timing && ctx->ev_ready; }
+    void begin(cudaStream_t s)
+    {
+        if (on()) cudaEventRecord(ctx->ev[2 * used], s);
+    }
+    void end(cudaStream_t s, int kind)
+    {
+        if (!on()) return;
+        cudaEventRecord(ctx->ev[2 * used + 1], s);
+        kinds[used++] = kind;
+    }
+    // after the stream has been synchronised
+    void collect()
+    {
+        for (int q = 0; q < used; ++q) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]) == cudaSuccess) {
+                ctx->phase_ms[kinds[q]] += ms;
+                ctx->phase_count[kinds[q]] += 1;
+            }
+        }
+        used = 0;
+    }
+};
+
 // [reset] [init_r] [init B] WHILE{A, B} [finalize], all on the stream.
 template <typename T>
 static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_iter, bool do_init_r)
@@ -724,19 +760,37 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
         k_init_r<T><<<run.grid_s, kThreads, 0, s>>>(run.d_desc);
         GMAF_CUDA(cudaGetLastError());
     }
-    if (!ctx->no_graph) return cuda_status(cudaGraphLaunch(gc.exec, s));
+    if (use_graph(ctx)) {
+        if (!run.h.use_cond) return GMAF_CUDA_ERROR;   // descriptor prepared for another mode
+        return cuda_status(cudaGraphLaunch(gc.exec, s));
+    }
+    if (run.h.use_cond) return GMAF_CUDA_ERROR;
     // host-chunked loop control: phases return at once after `done` is set
+    constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
+    const PcgDesc<T> *dd = run.d_desc;
     int *done_h = (int *)ctx->pinned;
-    launch_phase<T>(run, s, 0);
+    PhaseClock clk{ctx};
+    clk.begin(s);
+    k_phase_b<T, TX, TY, true><<<run.grid_b, kThreads, 0, s>>>(dd);
+    clk.end(s, 2);
     GMAF_CUDA(cudaGetLastError());
-    for (int it = 0; it <= run.h.max_iter + 16; it += 16) {
+    const int chunk = 16;
+    for (int it = 0; it <= run.h.max_iter + chunk; it += chunk) {
         GMAF_CUDA(cudaMemcpyAsync(done_h, &run.h.sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
         GMAF_CUDA(cudaStreamSynchronize(s));
+        clk.collect();
         if (*done_h) break;
-        for (int q = 0; q < 16; ++q) launch_phase<T>(run, s, 1);
+        for (int q = 0; q < chunk; ++q) {
+            clk.begin(s);
+            k_phase_a<T, TX, TY><<<run.grid_a, kThreads, 0, s>>>(dd);
+            clk.end(s, 0);
+            clk.begin(s);
+            k_phase_b<T, TX, TY, false><<<run.grid_b, kThreads, 0, s>>>(dd);
+            clk.end(s, 1);
+        }
         GMAF_CUDA(cudaGetLastError());
     }
-    launch_phase<T>(run, s, 2);
+    k_finalize<T><<<run.grid_s, kThreads, 0, s>>>(dd);
     return cuda_status(cudaGetLastError());
 }
 
@@ -831,9 +885,15 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
             GMAF_TRY(read_scalars(ctx, dsc, hsc));
             rd.r = h.r[hsc->iter & 1];
             GMAF_CUDA(cudaMemcpyAsync(d_rdesc, &rd, sizeof(ResidDesc), cudaMemcpyHostToDevice, s));
-            k_resid64<<<gs, kThreads, 0, s>>>(d_rdesc);
-            GMAF_CUDA(cudaGetLastError());
-            GMAF_TRY(read_scalars(ctx, dsc_outer, ho));
+            {
+                PhaseClock clk{ctx};
+                clk.begin(s);
+                k_resid64<<<gs, kThreads, 0, s>>>(d_rdesc);
+                clk.end(s, 3);
+                GMAF_CUDA(cudaGetLastError());
+                GMAF_TRY(read_scalars(ctx, dsc_outer, ho));
+                clk.collect();
+            }
             double true_rel = ho->true_rel;
             if (hsc->zero_rhs) {
                 GMAF_CUDA(cudaMemsetAsync(p, 0, (size_t)N * sizeof(double), s));
@@ -914,9 +974,15 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     int total_inner = 0, outer = 0;
     inf.status = GMAF_NOT_CONVERGED;
     for (;;) {
-        k_resid64<<<gs, kThreads, 0, s>>>(d_rdesc);
-        GMAF_CUDA(cudaGetLastError());
-        GMAF_TRY(read_scalars(ctx, dsc_outer, ho));
+        {
+            PhaseClock clk{ctx};
+            clk.begin(s);
+            k_resid64<<<gs, kThreads, 0, s>>>(d_rdesc);
+            clk.end(s, 3);
+            GMAF_CUDA(cudaGetLastError());
+            GMAF_TRY(read_scalars(ctx, dsc_outer, ho));
+            clk.collect();
+        }
         inf.true_rel_residual = ho->true_rel;
         inf.rel_residual = ho->true_rel;
         if (ho->status != 0 || !std::isfinite(ho->true_rel)) {

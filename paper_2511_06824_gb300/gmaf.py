@@ -30,7 +30,8 @@ GMAF_TIMEOUT = -7
 
 EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_bytes",
             "gmaf_last_solve_info", "gmaf_assemble", "gmaf_solve_joint", "gmaf_integrate_loads",
-            "gmaf_picard_step", "gmaf_status_string")
+            "gmaf_picard_step", "gmaf_status_string", "gmaf_set_phase_timing",
+            "gmaf_phase_timing")
 
 
 class gmaf_grid(ctypes.Structure):
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
                                    ctypes.c_double, _DP, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(gmaf_solver_opts), _DP, _DP, _DP,
                                    ctypes.POINTER(ctypes.c_int32)]
+    L.gmaf_set_phase_timing.argtypes = [_VP, ctypes.c_int]
+    L.gmaf_phase_timing.argtypes = [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]
     L.gmaf_status_string.argtypes = [ctypes.c_int]
     L.gmaf_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -272,6 +275,21 @@ def gmaf_picard_step(ctx: int, n_theta: int, n_z: int, phys, tex, st_vec, e_prev
     _check("gmaf_picard_step", rc, allow)
     return dict(status=rc, state=state_vector(s), loads=loads, J=J.reshape(6, 8), G=G,
                 iters=it.value)
+
+
+def gmaf_set_phase_timing(ctx: int, on: bool) -> None:
+    _check("gmaf_set_phase_timing", load().gmaf_set_phase_timing(_VP(ctx), 1 if on else 0))
+
+
+PHASES = ("phase_a", "phase_b", "init_b", "resid64")
+
+
+def gmaf_phase_timing(ctx: int) -> dict:
+    """{kind: (total_ms, launches)} for phase_a, phase_b, init_b, resid64."""
+    ms = np.zeros(4)
+    cnt = (ctypes.c_int64 * 4)()
+    _check("gmaf_phase_timing", load().gmaf_phase_timing(_VP(ctx), ms.ctypes.data_as(_DP), cnt))
+    return {k: (float(ms[q]), int(cnt[q])) for q, k in enumerate(PHASES)}
 
 
 class Context:

@@ -271,3 +271,29 @@ def test_picard_step_matches_oracle(g, ctx, nth, nz, textured, precision):
     np.testing.assert_allclose(r["G"], o["G"], rtol=1e-6, atol=1e-6 * np.abs(o["G"]).max())
     ds_g, ds_o = r["state"] - st0, o["state"] - st0
     assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o) + 1e-20
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_phase_timing_path_matches_graph_path(g, precision):
+    """Per-phase event timing drives the loop from the host; results are bitwise the
+    graph's and every phase launch is counted."""
+    conds = states(9, seed=13)
+    nth, nz = 140, 33
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
+    args = [dev(D), dev(aE), dev(aN), dev(S)]
+    n = 9 * nth * nz
+    opts = g.solver_opts(precision=precision)
+    c = g.Context()
+    p0 = zeros(n)
+    g.gmaf_solve_joint(c.handle, nth, nz, 9, *args, p0, opts)
+    g.gmaf_set_phase_timing(c.handle, True)
+    p1 = zeros(n)
+    st, it, rel = g.gmaf_solve_joint(c.handle, nth, nz, 9, *args, p1, opts)
+    t = g.gmaf_phase_timing(c.handle)
+    g.gmaf_set_phase_timing(c.handle, False)
+    p2 = zeros(n)
+    g.gmaf_solve_joint(c.handle, nth, nz, 9, *args, p2, opts)
+    c.close()
+    assert torch.equal(p0, p1) and torch.equal(p0, p2)
+    assert t["phase_a"][1] >= it and t["phase_b"][1] >= it and t["phase_a"][0] > 0
+    assert t["resid64"][1] >= 1
