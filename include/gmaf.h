@@ -186,6 +186,31 @@ int gmaf_picard_step(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *p
 int gmaf_set_phase_timing(gmaf_ctx *ctx, int on);
 int gmaf_phase_timing(const gmaf_ctx *ctx, double ms_out[4], int64_t launches_out[4]);
 
+/* Allocation-free joint solve.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory while they run, for
+ * example a solver plug-in inside a host program whose own pool allocator owns
+ * all of the GPU's memory and offers plug-ins no allocation hook, or a
+ * real-time co-simulation loop that cannot accept the latency, or the possible
+ * failure, of an allocation in the middle of a time step.  It computes what
+ * gmaf_solve_joint computes in FP64 mode (opts->precision must be 0), with the
+ * same arguments minus the context and plus the stream, and allocates nothing:
+ * its scratch is a fixed array of GMAF_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  A problem needs 131072 + 7 * ceil256(8 * n_cond * n_theta * n_z)
+ * bytes of it, so at most 1,795,200 joint unknowns (the 9-condition
+ * 512 x 256 batch fits);
+ * larger problems return GMAF_OUT_OF_MEMORY before any work is issued.
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * uses the same array and leaves its contents behind, so calls whose GPU work
+ * overlaps (different streams, threads or processes sharing the library on one
+ * device) race on it: serialise them.  Synchronises the stream. */
+#define GMAF_NOALLOC_SCRATCH_BYTES (96u * 1024u * 1024u)
+int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, const double *D,
+                             const double *aE, const double *aN, const double *S, double *p,
+                             const gmaf_solver_opts *opts, void *cuda_stream, int32_t *iters_out,
+                             double *rel_res_out);
+
 /* Static description of a status code. */
 const char *gmaf_status_string(int status);
 

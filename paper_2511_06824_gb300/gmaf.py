@@ -31,7 +31,7 @@ GMAF_TIMEOUT = -7
 EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_bytes",
             "gmaf_last_solve_info", "gmaf_assemble", "gmaf_solve_joint", "gmaf_integrate_loads",
             "gmaf_picard_step", "gmaf_status_string", "gmaf_set_phase_timing",
-            "gmaf_phase_timing")
+            "gmaf_phase_timing", "gmaf_solve_joint_noalloc")
 
 
 class gmaf_grid(ctypes.Structure):
@@ -104,6 +104,10 @@ def load(path: str = LIB_PATH):
                                    ctypes.POINTER(ctypes.c_int32)]
     L.gmaf_set_phase_timing.argtypes = [_VP, ctypes.c_int]
     L.gmaf_phase_timing.argtypes = [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]
+    L.gmaf_solve_joint_noalloc.argtypes = [ctypes.POINTER(gmaf_grid), ctypes.c_int32, _VP, _VP,
+                                           _VP, _VP, _VP, ctypes.POINTER(gmaf_solver_opts), _VP,
+                                           ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_double)]
     L.gmaf_status_string.argtypes = [ctypes.c_int]
     L.gmaf_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -290,6 +294,27 @@ def gmaf_phase_timing(ctx: int) -> dict:
     cnt = (ctypes.c_int64 * 4)()
     _check("gmaf_phase_timing", load().gmaf_phase_timing(_VP(ctx), ms.ctypes.data_as(_DP), cnt))
     return {k: (float(ms[q]), int(cnt[q])) for q, k in enumerate(PHASES)}
+
+
+def gmaf_solve_joint_noalloc(n_theta: int, n_z: int, n_cond: int, D, aE, aN, S, p,
+                             opts: Optional[gmaf_solver_opts] = None, stream=None,
+                             allow=(GMAF_OK,)):
+    """FP64 joint solve that allocates no device memory (scratch is a fixed array
+    inside the library).  Returns (status, iterations, true relative residual)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    n = n_cond * n_theta * n_z
+    g = grid(n_theta, n_z)
+    o = opts or solver_opts()
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = load().gmaf_solve_joint_noalloc(ctypes.byref(g), int(n_cond), _dev(D, n, "D"),
+                                         _dev(aE, n, "aE"), _dev(aN, n, "aN"), _dev(S, n, "S"),
+                                         _dev(p, n, "p"), ctypes.byref(o), _VP(stream),
+                                         ctypes.byref(it), ctypes.byref(rel))
+    _check("gmaf_solve_joint_noalloc", st, allow)
+    return st, it.value, rel.value
 
 
 class Context:

@@ -1,0 +1,78 @@
+"""The allocation-free joint solve against the ordinary one.
+
+Some programs that call this library may not allocate device memory while
+they run: a host application whose own pool allocator owns all of the GPU's
+memory and gives solver plug-ins no allocation hook, or a real-time
+co-simulation loop that cannot accept the latency, or the possible failure, of
+an allocation in the middle of a time step.  gmaf_solve_joint_noalloc serves
+them with a fixed scratch array inside the library.  This test calls it through
+the C ABI twice in a row, on two different problems, and checks each result
+against gmaf_solve_joint (pressure relative L2 1e-9, the FP64 parity bound of
+the other tests); a problem larger than the array must be refused.
+
+The file name puts it last in collection order, so that a run stopping at the
+first failure has run every other test before this one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_06824_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PHYS = inputs.phys_vector()
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_06824_gb300 import build, gmaf
+    build.build()
+    gmaf.load()
+    return gmaf
+
+
+def _problem(nth, nz, K, seed, textured):
+    rng = np.random.default_rng(seed)
+    tex = inputs.dimple_texture(rng) if textured else inputs.smooth_texture()
+    conds = [inputs.random_state(rng) for _ in range(K)]
+    st, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex, conds)
+    assert st == 0
+    return [torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda() for a in (D, aE, aN, S)]
+
+
+def test_noalloc_solve_matches_solve_joint_twice_in_a_row(g):
+    cases = [(150, 60, 9, 1, True), (64, 32, 3, 2, False)]
+    ctx = g.Context()
+    try:
+        for nth, nz, K, seed, textured in cases:
+            D, aE, aN, S = _problem(nth, nz, K, seed, textured)
+            n = K * nth * nz
+            p_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+            p_na = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
+            opts = g.solver_opts(eps=1e-10)
+            st, it_ref, rel_ref = g.gmaf_solve_joint(ctx.handle, nth, nz, K, D, aE, aN, S, p_ref,
+                                                     opts)
+            st2, it_na, rel_na = g.gmaf_solve_joint_noalloc(nth, nz, K, D, aE, aN, S, p_na, opts)
+            assert st == 0 and st2 == 0
+            assert it_na == it_ref
+            assert rel_na <= 1e-9
+            a, b = p_na.cpu().numpy(), p_ref.cpu().numpy()
+            assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
+    finally:
+        ctx.close()
+
+
+def test_noalloc_refuses_problems_beyond_its_scratch(g):
+    n_theta, n_z, K = 2048, 1024, 9
+    small = torch.zeros(64 * 32, dtype=torch.float64, device="cuda")
+    big = torch.zeros(n_theta * n_z * K, dtype=torch.float64, device="cuda")
+    st, it, rel = g.gmaf_solve_joint_noalloc(n_theta, n_z, K, big, big, big, big, big,
+                                             allow=(g.GMAF_OUT_OF_MEMORY,))
+    assert st == g.GMAF_OUT_OF_MEMORY
+    with pytest.raises(g.GmafError):
+        g.gmaf_solve_joint_noalloc(64, 32, 1, small, small, small, small, small,
+                                   g.solver_opts(precision=1))
