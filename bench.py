@@ -213,7 +213,9 @@ def run_ours(args):
         for _ in range(K):
             r = step(opts)
             its.append(r["iters"])
-            outer.append(gmaf.gmaf_last_solve_info(ctx.handle)["outer_iterations"])
+            info = gmaf.gmaf_last_solve_info(ctx.handle)
+            outer.append(info["outer_iterations"])
+        timed.info = info
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -303,6 +305,7 @@ def run_ours(args):
         "picard_steps_per_s": picard_rate,
         "pcg_iterations_per_step": float(np.mean(its)),
         "outer_refinements_per_step": float(np.mean(outer)),
+        "kernel_variant": timed.info["kernel_variant"], "tasks_per_phase": timed.info["tasks"],
         "e2e": {"value": float(sum(its)) * w.dof * world / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "picard_steps_per_s": K * world / t_e2e},
@@ -331,6 +334,7 @@ def run_ours(args):
                        "value": float(sum(its64)) * w.dof * world / (ms64 / 1e3),
                        "picard_steps_per_s": K64 * world / (ms64 / 1e3),
                        "pcg_iterations_per_step": float(np.mean(its64)), "phases": p64,
+                       "kernel_variant": timed.info["kernel_variant"],
                        "note": "FP64 mode is bound by GB300's FP64 pipe, not by HBM"}
     ctx.close()
 

@@ -102,6 +102,10 @@ typedef struct {
     int32_t status;
     double rel_residual;       /* recurrence relative residual at exit (FP64 mode)       */
     double true_rel_residual;  /* ||S - A p|| / ||S|| at exit, in FP64                   */
+    int32_t kernel_variant;    /* PCG kernels used: 1000 VEC + 10 TY + MINB (columns per
+                                  lane, rows per task, blocks per SM); chosen per problem
+                                  shape by the autotuner on the first solve of that shape */
+    int32_t tasks;             /* strip x row-block x condition tasks per PCG phase       */
 } gmaf_solve_info;
 
 typedef struct gmaf_ctx gmaf_ctx;
@@ -196,8 +200,8 @@ int gmaf_phase_timing(const gmaf_ctx *ctx, double ms_out[4], int64_t launches_ou
  * same arguments minus the context and plus the stream, and allocates nothing:
  * its scratch is a fixed array of GMAF_NOALLOC_SCRATCH_BYTES inside the
  * library, which every GPU that loads the library holds until the process
- * exits.  A problem needs 131072 + 7 * ceil256(8 * n_cond * n_theta * n_z)
- * bytes of it, so at most 1,795,200 joint unknowns (the 9-condition
+ * exits.  A problem needs 1048576 + 7 * ceil256(8 * n_cond * n_theta * n_z)
+ * bytes of it, so at most 1,778,816 joint unknowns (the 9-condition
  * 512 x 256 batch fits);
  * larger problems return GMAF_OUT_OF_MEMORY before any work is issued.
  * The first call on each device looks up the array's device address (with that

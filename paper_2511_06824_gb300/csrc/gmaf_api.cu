@@ -131,6 +131,10 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     c->budget = hbm_budget_bytes;
     const char *ng = std::getenv("GMAF_NO_GRAPH");
     c->no_graph = (ng && ng[0] == '1') ? 1 : 0;
+    const char *nt = std::getenv("GMAF_NO_TUNE");
+    c->no_tune = (nt && nt[0] == '1') ? 1 : 0;
+    const char *fv = std::getenv("GMAF_VARIANT");
+    c->force_variant = fv ? std::atoi(fv) : -1;
     *out = c;
     return GMAF_OK;
 }

@@ -44,6 +44,7 @@ struct Scalars {
     int iter, first, done, converged, status, pending, guard, zero_rhs;
     int max_iter;
     unsigned int ticket[6];
+    unsigned int task_ctr[2];   // next task of phase A / phase B
 };
 
 enum Ticket { kTicketA = 0, kTicketB = 1, kTicketInit = 2, kTicketResid = 3, kTicketMisc = 4 };
@@ -62,7 +63,7 @@ struct PcgDesc {
     int max_iter;
     cudaGraphConditionalHandle cond;
     Scalars *sc;
-    double *partials;              // [2][grid]
+    double *partials;              // per-task sums [ntiles][2], or per-block [2][grid]
 };
 
 // FP64 residual r = S - A p over all conditions, with ||r||^2 and ||S||^2.
@@ -96,7 +97,15 @@ struct GraphCache {
     cudaGraphConditionalHandle handle = 0;
     int grid_a = 0, grid_b = 0, grid_s = 0;
     const void *desc = nullptr;
+    const void *ka = nullptr;      // phase-A kernel the graph was built with
 };
+
+// Autotuner decision for one solve shape.
+struct TuneEntry {
+    int tsize, nth, nz, K, precond, vec_ok;
+    int choice;
+};
+constexpr int kTuneEntries = 32;
 
 }  // namespace gmaf
 
@@ -117,6 +126,10 @@ struct gmaf_ctx {
     long long phase_count[4];
     cudaEvent_t ev[2 * 2 * 16 + 2];
     int ev_ready;
+    int no_tune;                   // GMAF_NO_TUNE=1: first candidate kernels, no tuning
+    int force_variant;             // GMAF_VARIANT=<id>: use that kernel variant when eligible
+    gmaf::TuneEntry tune[gmaf::kTuneEntries];
+    int ntune, tune_next;
 };
 
 namespace gmaf {

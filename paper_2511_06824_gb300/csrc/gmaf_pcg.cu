@@ -126,34 +126,203 @@ __device__ __forceinline__ int wrapi(int i, int n)
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
-// ------------------------------------------------------------------ tile geometry
+// ------------------------------------------------------------------ strip-marching tiles
+//
+// A task is one condition x one strip of W = 32 * VEC consecutive columns x TY
+// rows.  One warp owns a task: lane l holds columns i0 + l*VEC .. +VEC-1 (one
+// 16-byte vector per field and row) and the warp marches down the rows keeping
+// the rows above and below in registers; the theta neighbours of a row go
+// through a one-row shared buffer of the warp (slot s <-> column i0 - 2 + s in
+// phase B, i0 - 1 + s in phase A) filled by the owners and, for the halo
+// columns, by lanes 0..3.  Column indices are reduced modulo n_theta once per
+// task, so the periodic wrap costs nothing per cell; lanes whose columns lie
+// beyond n_theta compute the wrapped columns (their values are neighbours of the
+// owned ones) but store nothing.  Requires n_theta % VEC == 0 and 16-byte
+// aligned arrays for VEC > 1.
+//
+// Tasks are numbered with the condition fastest, so the warps working on one
+// spatial strip at the same time read a shared coefficient slot once from DRAM.
 
-template <int TX, int TY>
-struct TileOf {
-    int cond, i0, j0;
+constexpr int kWarps = kThreads / 32;
+
+template <typename T, int VEC>
+struct Vec;
+template <typename T>
+struct Vec<T, 1> {
+    static __device__ __forceinline__ void ld(const T *p, T (&x)[1]) { x[0] = __ldg(p); }
+    static __device__ __forceinline__ void ldrw(const T *p, T (&x)[1]) { x[0] = *p; }
+    static __device__ __forceinline__ void st(T *p, const T (&x)[1]) { *p = x[0]; }
+};
+template <>
+struct Vec<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[4])
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    }
+    static __device__ __forceinline__ void ldrw(const float *p, float (&x)[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+template <>
+struct Vec<float, 2> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[2])
+    {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void ldrw(const float *p, float (&x)[2])
+    {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[2])
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    }
+};
+template <>
+struct Vec<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double (&x)[2])
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void ldrw(const double *p, double (&x)[2])
+    {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&x)[2])
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
+    }
 };
 
-template <int TX, int TY>
-__device__ __forceinline__ TileOf<TX, TY> tile_of(long long t, int K, int tiles_x)
+// Dot-product accumulation: a row's VEC products are summed in T, the row sums
+// are accumulated with Acc<T> (exact two-float form for float), and the totals
+// are reduced in FP64 across lanes and blocks.
+template <typename T>
+struct RowAcc {
+    Acc<T> acc;
+    __device__ __forceinline__ void add_row(T s) { acc.add(s, T(1)); }
+    __device__ __forceinline__ double value() const { return acc.value(); }
+};
+
+struct Task {
+    int cond, i0, j0, jend;
+};
+
+template <int W, int TY>
+__device__ __forceinline__ Task task_of(long long t, int K, int tiles_x, int nz)
 {
-    TileOf<TX, TY> r;
-    r.cond = (int)(t % K);          // conditions of one spatial tile are adjacent,
-    const long long sp = t / K;     // so coefficient slots shared by several
-    const int ty = (int)(sp / tiles_x);   // conditions are re-read from L2
+    Task r;
+    r.cond = (int)(t % K);
+    const long long sp = t / K;
+    const int ty = (int)(sp / tiles_x);
     const int tx = (int)(sp - (long long)ty * tiles_x);
-    r.i0 = tx * TX;
+    r.i0 = tx * W;
     r.j0 = ty * TY;
+    r.jend = min(r.j0 + TY, nz);
     return r;
 }
 
-// ------------------------------------------------------------------ phase A
-
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(kThreads) k_phase_a(const PcgDesc<T> *__restrict__ dp)
+__device__ __forceinline__ int wrap_col(int c, int n)
 {
+    int r = c % n;
+    return r < 0 ? r + n : r;
+}
+
+// Next task of the warp from the kernel's task counter (one atomic per task).
+__device__ __forceinline__ unsigned next_task(unsigned *ctr, int lane)
+{
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(ctr, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// Publish NV per-task sums (warp-reduced in a fixed order) at partials[t * NV + q].
+template <int NV>
+__device__ __forceinline__ void publish_task(const double (&v)[NV], double *partials, unsigned t,
+                                             int lane)
+{
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const double s = warp_sum_d(v[q]);
+        if (lane == 0) partials[(size_t)t * NV + q] = s;
+    }
+}
+
+// After every task of the launch is published: the last block (by ticket)
+// adds the per-task sums in task order, so the totals depend neither on the
+// grid nor on which warp ran which task.  Also rearms the task counter.
+template <int NV>
+__device__ __forceinline__ bool reduce_tasks(const double *partials, unsigned ntasks,
+                                             unsigned *ticket, unsigned *task_ctr,
+                                             double (&tot)[NV])
+{
+    __shared__ double red[NV][32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (unsigned t = threadIdx.x; t < ntasks; t += blockDim.x)
+            s += __ldcg(&partials[(size_t)t * NV + q]);
+        s = warp_sum_d(s);
+        if (lane == 0) red[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[q][w];
+            tot[q] = t;
+        }
+        *ticket = 0u;
+        *task_ctr = 0u;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ phase A
+//   p += alpha' u';  u = z + beta u';  v = A u;  partial u.v
+// Marching: at row jr the warp forms u(jr) and outputs v(jr - 1), which needs
+// u(jr - 2) (register), u(jr - 1) and its row neighbours (shared row) and u(jr).
+// The loads of row jr + 1 are issued before row jr is processed.
+// Shared row slot s holds column i0 - 4 + s (own columns start 16-byte aligned).
+
+template <typename T, int VEC>
+struct RowA {
+    T z[VEC], uo[VEC], D[VEC], e[VEC], n[VEC], p[VEC];
+    T hz, huo, he;
+};
+
+template <typename T, int VEC, int TY, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__restrict__ dp)
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8;
     const PcgDesc<T> &d = *dp;
     Scalars *sc = d.sc;
-    __shared__ T su[TY + 2][TX + 2];
+    __shared__ __align__(16) T su[kWarps][NB];
+    __shared__ __align__(16) T sa[kWarps][NB];
     __shared__ int s_done, s_k, s_first;
     __shared__ double s_alpha, s_beta;
     if (threadIdx.x == 0) {
@@ -170,56 +339,128 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(const PcgDesc<T> *__restri
     }
     __syncthreads();
     if (s_done) return;
-    const int k = s_k, first = s_first;
+    const int k = s_k;
+    const bool first = s_first != 0;
     const T alpha_prev = (T)s_alpha, beta = (T)s_beta;
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *ub = su[wp];
+    T *ab = sa[wp];
     const T *uo_base = d.u[(k + 1) & 1];
     T *un_base = d.u[k & 1];
-    Acc<T> acc;
-    for (long long t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
-        const TileOf<TX, TY> tl = tile_of<TX, TY>(t, d.K, d.tiles_x);
-        const size_t off = (size_t)tl.cond * (size_t)n;
-        const size_t coff = (size_t)d.cslot[tl.cond] * (size_t)n;
+    const unsigned ntasks = (unsigned)d.ntiles;
+    for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
+         t = next_task(&sc->task_ctr[0], lane)) {
+        RowAcc<T> acc;
+        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, nz);
+        const size_t off = (size_t)tk.cond * (size_t)n;
+        const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
         const T *z = d.z + off;
         const T *uo = uo_base + off;
-        for (int l = threadIdx.x; l < (TY + 2) * (TX + 2); l += kThreads) {
-            const int rr = l / (TX + 2), cc = l - rr * (TX + 2);
-            const int gj = tl.j0 - 1 + rr;
-            const int gi = wrapi(tl.i0 - 1 + cc, nth);
-            T val = T(0);
-            if (gj >= 0 && gj < nz) {
-                const size_t q = (size_t)gj * nth + gi;
-                val = first ? z[q] : z[q] + beta * uo[q];
+        T *un = un_base + off;
+        T *vv = d.v + off;
+        T *pp = d.p + off;
+        const T *D = d.D + coff;
+        const T *aE = d.aE + coff;
+        const T *aN = d.aN + coff;
+        const int c0 = tk.i0 + lane * VEC;
+        const bool owned = c0 < nth;
+        const int g0 = wrap_col(c0, nth);
+        const int sown = 4 + lane * VEC;
+        // halo: lane 0 -> column i0 - 1 (slot 3), lane 1 -> column i0 + W (slot W + 4)
+        const int hg = wrap_col(lane == 0 ? tk.i0 - 1 : tk.i0 + W, nth);
+        const int hslot = lane == 0 ? 3 : W + 4;
+
+        auto load_row = [&](int jr, RowA<T, VEC> &R) {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) R.z[q] = R.uo[q] = R.D[q] = R.e[q] = R.n[q] = R.p[q] = T(0);
+            R.hz = R.huo = R.he = T(0);
+            if (jr < 0 || jr >= nz) return;
+            const size_t q0 = (size_t)jr * nth + g0;
+            Vec<T, VEC>::ld(z + q0, R.z);
+            if (!first) Vec<T, VEC>::ld(uo + q0, R.uo);
+            Vec<T, VEC>::ld(aN + q0, R.n);
+            if (jr >= tk.j0 && jr < tk.jend) {
+                Vec<T, VEC>::ld(D + q0, R.D);
+                Vec<T, VEC>::ld(aE + q0, R.e);
+                if (!first && owned) Vec<T, VEC>::ldrw(pp + q0, R.p);
             }
-            su[rr][cc] = val;
-        }
-        __syncthreads();
-        for (int l = threadIdx.x; l < TY * TX; l += kThreads) {
-            const int tj = l / TX, ti = l - tj * TX;
-            const int gj = tl.j0 + tj, gi = tl.i0 + ti;
-            if (gj < nz && gi < nth) {
-                const size_t q = (size_t)gj * nth + gi;
-                const size_t row = coff + (size_t)gj * nth;
-                const T uc = su[tj + 1][ti + 1];
-                const T dd = d.D[coff + q];
-                const T ae = d.aE[coff + q];
-                const T aw = d.aE[row + (gi == 0 ? nth - 1 : gi - 1)];
-                const T an = d.aN[coff + q];
-                const T as = gj > 0 ? d.aN[coff + q - nth] : T(0);
-                const T vv = dd * uc - ae * su[tj + 1][ti + 2] - aw * su[tj + 1][ti] -
-                             an * su[tj + 2][ti + 1] - as * su[tj][ti + 1];
-                un_base[off + q] = uc;
-                d.v[off + q] = vv;
-                if (!first) d.p[off + q] += alpha_prev * uo[q];
-                acc.add(uc, vv);
+            if (lane < 2) {
+                const size_t qh = (size_t)jr * nth + hg;
+                R.hz = __ldg(z + qh);
+                if (!first) R.huo = __ldg(uo + qh);
+                if (lane == 0) R.he = __ldg(aE + qh);
+            }
+        };
+
+        T u_m1[VEC], u_m2[VEC], uo_m1[VEC], D_m1[VEC], e_m1[VEC], n_m1[VEC], n_m2[VEC], p_m1[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q)
+            u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = T(0);
+        RowA<T, VEC> nx;
+        load_row(tk.j0 - 1, nx);
+        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+            const RowA<T, VEC> cur = nx;
+            if (jr + 1 <= tk.jend) load_row(jr + 1, nx);
+            T u[VEC];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) u[q] = first ? cur.z[q] : cur.z[q] + beta * cur.uo[q];
+            const T hu = first ? cur.hz : cur.hz + beta * cur.huo;
+            // output row jo = jr - 1: its u row and aE row are in the shared buffers
+            const int jo = jr - 1;
+            if (jo >= tk.j0 && jo < tk.jend) {
+                T vout[VEC];
+                T rowsum = T(0);
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const int s = sown + q;
+                    const T uE = (q < VEC - 1) ? u_m1[q + 1] : ub[s + 1];
+                    const T uW = (q > 0) ? u_m1[q - 1] : ub[s - 1];
+                    const T aW = (q > 0) ? e_m1[q - 1] : ab[s - 1];
+                    vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
+                              n_m2[q] * u_m2[q];
+                    rowsum += u_m1[q] * vout[q];
+                }
+                if (owned) {
+                    const size_t qo = (size_t)jo * nth + g0;
+                    Vec<T, VEC>::st(un + qo, u_m1);
+                    Vec<T, VEC>::st(vv + qo, vout);
+                    if (!first) {
+                        T pn[VEC];
+#pragma unroll
+                        for (int q = 0; q < VEC; ++q) pn[q] = p_m1[q] + alpha_prev * uo_m1[q];
+                        Vec<T, VEC>::st(pp + qo, pn);
+                    }
+                    acc.add_row(rowsum);
+                }
+            }
+            __syncwarp();
+            Vec<T, VEC>::st(ub + sown, u);
+            Vec<T, VEC>::st(ab + sown, cur.e);
+            if (lane < 2) {
+                ub[hslot] = hu;
+                if (lane == 0) ab[hslot] = cur.he;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                u_m2[q] = u_m1[q];
+                u_m1[q] = u[q];
+                uo_m1[q] = cur.uo[q];
+                n_m2[q] = n_m1[q];
+                n_m1[q] = cur.n[q];
+                D_m1[q] = cur.D[q];
+                e_m1[q] = cur.e[q];
+                p_m1[q] = cur.p[q];
             }
         }
-        __syncthreads();
+        const double val[1] = {acc.value()};
+        publish_task<1>(val, d.partials, t, lane);
     }
-    double val[1] = {acc.value()};
     double tot[1];
-    if (reduce_last<1>(val, d.partials, &sc->ticket[kTicketA], tot) && threadIdx.x == 0) {
+    if (reduce_tasks<1>(d.partials, ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
+        threadIdx.x == 0) {
         const double uv = tot[0];
         sc->pending = 0;
         if (!finite_d(uv) || !(uv > 0.0) || !finite_d(sc->d)) {
@@ -232,15 +473,31 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(const PcgDesc<T> *__restri
 }
 
 // ------------------------------------------------------------------ phase B
+//   r -= alpha v;  z = M^-1 r;  partial r.z, r.r
+// Marching: at row jr the warp forms r(jr), y = D^-1 r (shared row), the first
+// ASSOR pass w(jr) (needs y(jr - 1) in registers and the row neighbours of
+// y(jr)), and the second pass z(jr - 1) (needs w(jr) in registers and the row
+// neighbours of w(jr - 1), still in the shared row).  Halo columns i0 - 2 ..
+// i0 - 1 and i0 + W .. i0 + W + 1 are formed by lanes 0..3.  The loads of row
+// jr + 1 are issued before row jr is processed.  Shared row slot s holds column
+// i0 - 4 + s.
 
-template <typename T, int TX, int TY, bool INIT>
-__global__ void __launch_bounds__(kThreads) k_phase_b(const PcgDesc<T> *__restrict__ dp)
+template <typename T, int VEC>
+struct RowB {
+    T r[VEC], v[VEC], dI[VEC], e[VEC], n[VEC];
+    T hr, hv, hd, he, hn;
+};
+
+template <typename T, int VEC, int TY, int MINB, bool INIT>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__restrict__ dp)
 {
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8;
     const PcgDesc<T> &d = *dp;
     Scalars *sc = d.sc;
-    __shared__ T sy[TY + 2][TX + 4];   // D^-1 r on the tile, halo: 1 row each side,
-    __shared__ T sw[TY + 2][TX + 4];   // 2 columns west, 2 east (column c <-> i0 - 2 + c)
-    __shared__ T sr[TY][TX];
+    __shared__ __align__(16) T sy[kWarps][NB];
+    __shared__ __align__(16) T sw[kWarps][NB];
+    __shared__ __align__(16) T sa[kWarps][NB];
     __shared__ int s_done, s_k;
     __shared__ double s_alpha;
     if (threadIdx.x == 0) {
@@ -255,85 +512,159 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(const PcgDesc<T> *__restri
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
     const T omega = d.omega, c1 = d.c1;
+    const bool assor = (d.precond == 1);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *yb = sy[wp];
+    T *wb = sw[wp];
+    T *ab = sa[wp];
     const T *ro_base = d.r[k & 1];
     T *rn_base = d.r[(k + 1) & 1];
-    const bool assor = (d.precond == 1);
-    Acc<T> arz, arr;
-    for (long long t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
-        const TileOf<TX, TY> tl = tile_of<TX, TY>(t, d.K, d.tiles_x);
-        const size_t off = (size_t)tl.cond * (size_t)n;
-        const size_t coff = (size_t)d.cslot[tl.cond] * (size_t)n;
+    const unsigned ntasks = (unsigned)d.ntiles;
+    for (unsigned t = next_task(&sc->task_ctr[1], lane); t < ntasks;
+         t = next_task(&sc->task_ctr[1], lane)) {
+        RowAcc<T> arz, arr;
+        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, nz);
+        const size_t off = (size_t)tk.cond * (size_t)n;
+        const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
         const T *ro = ro_base + off;
         const T *vv = d.v + off;
+        T *rn = rn_base + off;
+        T *zo = d.z + off;
         const T *invD = d.invD + coff;
         const T *aE = d.aE + coff;
         const T *aN = d.aN + coff;
-        // r_new and y = D^-1 r_new on the tile and its halo
-        for (int l = threadIdx.x; l < (TY + 2) * (TX + 4); l += kThreads) {
-            const int rr = l / (TX + 4), cc = l - rr * (TX + 4);
-            const int gj = tl.j0 - 1 + rr;
-            const int gi = wrapi(tl.i0 - 2 + cc, nth);
-            T y = T(0);
-            if (gj >= 0 && gj < nz) {
-                const size_t q = (size_t)gj * nth + gi;
-                const T r = INIT ? ro[q] : ro[q] - alpha * vv[q];
-                y = r * invD[q];
-                const int tj = rr - 1, ti = cc - 2;
-                if (tj >= 0 && tj < TY && ti >= 0 && ti < TX) sr[tj][ti] = r;
+        const int c0 = tk.i0 + lane * VEC;
+        const bool owned = c0 < nth;
+        const int g0 = wrap_col(c0, nth);
+        const int sown = 4 + lane * VEC;
+        // halo: lanes 0..3 -> columns i0-2, i0-1 (slots 2, 3), i0+W, i0+W+1 (slots W+4, W+5)
+        const int hoff = lane < 2 ? lane - 2 : W + (lane - 2);
+        const int hg = wrap_col(tk.i0 + hoff, nth);
+        const int hslot = lane < 2 ? lane + 2 : W + 2 + lane;
+
+        auto load_row = [&](int jr, RowB<T, VEC> &R) {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) R.r[q] = R.v[q] = R.dI[q] = R.e[q] = R.n[q] = T(0);
+            R.hr = R.hv = R.hd = R.he = R.hn = T(0);
+            if (jr < 0 || jr >= nz) return;
+            const size_t q0 = (size_t)jr * nth + g0;
+            Vec<T, VEC>::ld(ro + q0, R.r);
+            if (!INIT) Vec<T, VEC>::ld(vv + q0, R.v);
+            Vec<T, VEC>::ld(invD + q0, R.dI);
+            Vec<T, VEC>::ld(aE + q0, R.e);
+            Vec<T, VEC>::ld(aN + q0, R.n);
+            if (lane < 4) {
+                const size_t qh = (size_t)jr * nth + hg;
+                R.hr = __ldg(ro + qh);
+                if (!INIT) R.hv = __ldg(vv + qh);
+                R.hd = __ldg(invD + qh);
+                R.he = __ldg(aE + qh);
+                R.hn = __ldg(aN + qh);
             }
-            sy[rr][cc] = y;
-        }
-        __syncthreads();
-        if (assor) {
-            // first ASSOR pass (Eq. 3.5): w = y + omega D^-1 sum_{lower} a y on the tile
-            // plus the north row and the east/west columns the second pass reads
-            for (int l = threadIdx.x; l < (TY + 1) * (TX + 2); l += kThreads) {
-                const int rr = 1 + l / (TX + 2), cc = 1 + (l - (l / (TX + 2)) * (TX + 2));
-                const int gj = tl.j0 - 1 + rr;
-                const int gi = wrapi(tl.i0 - 2 + cc, nth);
-                T w = T(0);
-                if (gj < nz) {
-                    const size_t q = (size_t)gj * nth + gi;
-                    const size_t row = (size_t)gj * nth;
-                    T s = T(0);
-                    if (gj > 0) s += aN[q - nth] * sy[rr - 1][cc];
-                    if (gi > 0) s += aE[row + gi - 1] * sy[rr][cc - 1];
-                    if (gi == nth - 1) s += aE[q] * sy[rr][cc + 1];
-                    w = sy[rr][cc] + omega * invD[q] * s;
+        };
+
+        T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
+        T hy_m1 = T(0), hn_m1 = T(0);
+        RowB<T, VEC> nx;
+        load_row(tk.j0 - 1, nx);
+        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+            const RowB<T, VEC> cur = nx;
+            if (jr + 1 <= tk.jend) load_row(jr + 1, nx);
+            const bool inrow = jr >= 0 && jr < nz;
+            T r1[VEC], y[VEC];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                r1[q] = INIT ? cur.r[q] : cur.r[q] - alpha * cur.v[q];
+                y[q] = r1[q] * cur.dI[q];
+            }
+            const T hy = (INIT ? cur.hr : cur.hr - alpha * cur.hv) * cur.hd;
+            Vec<T, VEC>::st(yb + sown, y);
+            Vec<T, VEC>::st(ab + sown, cur.e);
+            if (lane < 4) {
+                yb[hslot] = hy;
+                ab[hslot] = cur.he;
+            }
+            __syncwarp();
+            // first ASSOR pass on row jr: w = y + omega D^-1 (lower couplings) y
+            T w[VEC];
+            T hw = T(0);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) w[q] = T(0);
+            if (assor && inrow && jr >= tk.j0) {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const int s = sown + q, gi = g0 + q;
+                    T sum = T(0);
+                    if (jr > 0) sum += n_m1[q] * y_m1[q];                            // south
+                    if (gi > 0)                                                        // west
+                        sum += ((q > 0) ? cur.e[q - 1] : ab[s - 1]) * ((q > 0) ? y[q - 1] : yb[s - 1]);
+                    if (gi == nth - 1) sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);  // east, wrapped
+                    w[q] = y[q] + omega * cur.dI[q] * sum;
                 }
-                sw[rr][cc] = w;
-            }
-            __syncthreads();
-        }
-        // second pass (Eq. 3.6) and the dot products
-        for (int l = threadIdx.x; l < TY * TX; l += kThreads) {
-            const int tj = l / TX, ti = l - tj * TX;
-            const int gj = tl.j0 + tj, gi = tl.i0 + ti;
-            if (gj < nz && gi < nth) {
-                const size_t q = (size_t)gj * nth + gi;
-                const int rr = tj + 1, cc = ti + 2;
-                T zz;
-                if (assor) {
-                    T s = T(0);
-                    if (gj < nz - 1) s += aN[q] * sw[rr + 1][cc];
-                    if (gi < nth - 1) s += aE[q] * sw[rr][cc + 1];
-                    if (gi == 0) s += aE[(size_t)gj * nth + nth - 1] * sw[rr][cc - 1];
-                    zz = c1 * (sw[rr][cc] + omega * invD[q] * s);
-                } else {
-                    zz = sy[rr][cc];
+                if (lane == 1 || lane == 2) {
+                    const int s = hslot;
+                    T sum = T(0);
+                    if (jr > 0) sum += hn_m1 * hy_m1;
+                    if (hg > 0) sum += ab[s - 1] * yb[s - 1];
+                    if (hg == nth - 1) sum += cur.he * yb[s + 1];
+                    hw = hy + omega * cur.hd * sum;
                 }
-                const T r = sr[tj][ti];
-                d.z[off + q] = zz;
-                if (!INIT) rn_base[off + q] = r;
-                arz.add(r, zz);
-                arr.add(r, r);
             }
+            // second pass on row jo = jr - 1: z = c1 (w + omega D^-1 (upper couplings) w)
+            const int jo = jr - 1;
+            if (jo >= tk.j0 && jo < tk.jend) {
+                T zz[VEC];
+                T rz = T(0), rr = T(0);
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    if (assor) {
+                        const int s = sown + q, gi = g0 + q;
+                        T sum = T(0);
+                        if (jo < nz - 1) sum += n_m1[q] * w[q];                                          // north
+                        if (gi < nth - 1) sum += e_m1[q] * ((q < VEC - 1) ? w_m1[q + 1] : wb[s + 1]);    // east
+                        if (gi == 0)                                                                     // west, wrapped
+                            sum += __ldg(aE + (size_t)jo * nth + nth - 1) * ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
+                        zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
+                    } else {
+                        zz[q] = y_m1[q];
+                    }
+                    rz += r_m1[q] * zz[q];
+                    rr += r_m1[q] * r_m1[q];
+                }
+                if (owned) {
+                    const size_t qo = (size_t)jo * nth + g0;
+                    Vec<T, VEC>::st(zo + qo, zz);
+                    if (!INIT) Vec<T, VEC>::st(rn + qo, r_m1);
+                    arz.add_row(rz);
+                    arr.add_row(rr);
+                }
+            }
+            __syncwarp();
+            if (assor) {
+                Vec<T, VEC>::st(wb + sown, w);
+                if (lane == 1 || lane == 2) wb[hslot] = hw;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                y_m1[q] = y[q];
+                w_m1[q] = w[q];
+                d_m1[q] = cur.dI[q];
+                n_m1[q] = cur.n[q];
+                e_m1[q] = cur.e[q];
+                r_m1[q] = r1[q];
+            }
+            hy_m1 = hy;
+            hn_m1 = cur.hn;
         }
-        __syncthreads();
+        const double val[2] = {arz.value(), arr.value()};
+        publish_task<2>(val, d.partials, t, lane);
     }
-    double val[2] = {arz.value(), arr.value()};
     double tot[2];
-    if (reduce_last<2>(val, d.partials, &sc->ticket[kTicketB], tot) && threadIdx.x == 0) {
+    if (reduce_tasks<2>(d.partials, ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
+        threadIdx.x == 0) {
         const double rz = tot[0], rr = tot[1];
         const double rel = sqrt(rr) / sc->normS;
         sc->rel = rel;
@@ -457,6 +788,8 @@ __global__ void k_reset(Scalars *sc, int keep_iter)
     sc->alpha = 0.0;
     sc->beta = 0.0;
     for (int q = 0; q < 6; ++q) sc->ticket[q] = 0u;
+    sc->task_ctr[0] = 0u;
+    sc->task_ctr[1] = 0u;
 }
 
 // ------------------------------------------------------------------ FP64 residual, conversions
@@ -547,17 +880,6 @@ __global__ void k_update_p64(double *__restrict__ p, const float *__restrict__ x
 
 // ------------------------------------------------------------------ host driver
 
-template <typename T>
-struct TileCfg;
-template <>
-struct TileCfg<double> {
-    static constexpr int TX = 128, TY = 8;
-};
-template <>
-struct TileCfg<float> {
-    static constexpr int TX = 128, TY = 16;
-};
-
 static int grid_for(const void *kernel, long long work_items, int num_sms)
 {
     int per_sm = 0;
@@ -587,31 +909,95 @@ static int stream_grid(long long N, int num_sms)
 
 #define GMAF_CUDA(x) GMAF_TRY(cuda_status(x))
 
+// The phase kernels of one run: strip width W = 32 * VEC, TY rows per task,
+// MINB blocks per SM requested from the register allocator.
+template <typename T>
+struct KernelSet {
+    const void *a, *b, *b_init;
+    int W, TY, id;
+};
+
+template <typename T, int VEC, int TY, int MINB>
+static KernelSet<T> ks_of(int)
+{
+    return {(const void *)k_phase_a<T, VEC, TY, MINB>,
+            (const void *)k_phase_b<T, VEC, TY, MINB, false>,
+            (const void *)k_phase_b<T, VEC, TY, MINB, true>, 32 * VEC, TY,
+            1000 * VEC + 10 * TY + MINB};
+}
+
+constexpr int kMaxVariants = 8;
+
+// Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
+static int variants(KernelSet<float> *out, bool vec_ok)
+{
+    int n = 0;
+    if (vec_ok) {
+        out[n++] = ks_of<float, 4, 32, 2>(0);
+        out[n++] = ks_of<float, 4, 16, 2>(0);
+        out[n++] = ks_of<float, 4, 16, 3>(1);
+        out[n++] = ks_of<float, 2, 32, 4>(2);
+        out[n++] = ks_of<float, 2, 16, 4>(3);
+    }
+    out[n++] = ks_of<float, 1, 32, 4>(4);
+    out[n++] = ks_of<float, 1, 16, 4>(5);
+    return n;
+}
+
+static int variants(KernelSet<double> *out, bool vec_ok)
+{
+    int n = 0;
+    if (vec_ok) {
+        out[n++] = ks_of<double, 2, 32, 2>(0);
+        out[n++] = ks_of<double, 2, 16, 2>(0);
+        out[n++] = ks_of<double, 2, 16, 3>(1);
+    }
+    out[n++] = ks_of<double, 1, 32, 3>(4);
+    out[n++] = ks_of<double, 1, 16, 3>(5);
+    return n;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+static bool vec_ok(const PcgDesc<T> &h)
+{
+    constexpr int V = sizeof(T) == 4 ? 4 : 2;
+    bool ok = (h.nth % V) == 0;
+    const void *ptrs[] = {h.D, h.invD, h.aE, h.aN, h.p, h.z, h.v, h.u[0], h.u[1], h.r[0], h.r[1]};
+    for (const void *q : ptrs) ok = ok && aligned16(q);
+    return ok;
+}
+
+// Default choice without tuning: the first candidate.
+template <typename T>
+static KernelSet<T> choose_kernels(const PcgDesc<T> &h)
+{
+    KernelSet<T> c[kMaxVariants];
+    variants(c, vec_ok(h));
+    return c[0];
+}
+
 template <typename T>
 struct PcgRun {
     PcgDesc<T> *d_desc;     // device copy of h
     PcgDesc<T> h;
+    KernelSet<T> ks;
     int grid_a, grid_b, grid_s;
 };
 
 template <typename T>
-static void launch_phase(const PcgRun<T> &run, cudaStream_t s, int which)
+static cudaError_t launch(const void *fn, int grid, const PcgDesc<T> *dd, cudaStream_t s)
 {
-    constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
-    const PcgDesc<T> *dd = run.d_desc;
-    if (which == 0) {
-        k_phase_b<T, TX, TY, true><<<run.grid_b, kThreads, 0, s>>>(dd);
-    } else if (which == 1) {
-        k_phase_a<T, TX, TY><<<run.grid_a, kThreads, 0, s>>>(dd);
-        k_phase_b<T, TX, TY, false><<<run.grid_b, kThreads, 0, s>>>(dd);
-    } else {
-        k_finalize<T><<<run.grid_s, kThreads, 0, s>>>(dd);
-    }
+    void *args[] = {(void *)&dd};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
-static bool graph_matches(const GraphCache &gc, int ga, int gb, int gs, const void *desc)
+static bool graph_matches(const GraphCache &gc, int ga, int gb, int gs, const void *desc,
+                          const void *ka)
 {
-    return gc.exec && gc.grid_a == ga && gc.grid_b == gb && gc.grid_s == gs && gc.desc == desc;
+    return gc.exec && gc.grid_a == ga && gc.grid_b == gb && gc.grid_s == gs && gc.desc == desc &&
+           gc.ka == ka;
 }
 
 // Build and instantiate  [init B] -> WHILE{A -> B} -> [finalize]  for a launch
@@ -628,7 +1014,6 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     GMAF_CUDA(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
     cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0u, cudaGraphCondAssignDefault);
-    constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     const PcgDesc<T> *dd = run.d_desc;
     void *args[] = {(void *)&dd};
     cudaGraphNode_t n_init, n_while, n_fin, n_a, n_b;
@@ -636,7 +1021,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     kp.blockDim = dim3(kThreads);
     kp.kernelParams = args;
     if (e == cudaSuccess) {
-        kp.func = (void *)k_phase_b<T, TX, TY, true>;
+        kp.func = (void *)run.ks.b_init;
         kp.gridDim = dim3(run.grid_b);
         e = cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp);
     }
@@ -648,11 +1033,11 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     if (e == cudaSuccess) e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
     if (e == cudaSuccess) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
-        kp.func = (void *)k_phase_a<T, TX, TY>;
+        kp.func = (void *)run.ks.a;
         kp.gridDim = dim3(run.grid_a);
         e = cudaGraphAddKernelNode(&n_a, body, nullptr, 0, &kp);
         if (e == cudaSuccess) {
-            kp.func = (void *)k_phase_b<T, TX, TY, false>;
+            kp.func = (void *)run.ks.b;
             kp.gridDim = dim3(run.grid_b);
             e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
         }
@@ -673,31 +1058,129 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     gc.grid_b = run.grid_b;
     gc.grid_s = run.grid_s;
     gc.desc = run.d_desc;
+    gc.ka = run.ks.a;
     (void)s;
     return GMAF_OK;
 }
 
-// Launch shape, partial-sum buffer and descriptor slot of a run.
-template <typename T>
-static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
+// Blocks for a persistent phase kernel: enough to hold every task's warp, at
+// most what stays resident.
+static int phase_grid(const void *kernel, long long ntasks, int num_sms)
 {
-    constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
+    return grid_for(kernel, (ntasks + kWarps - 1) / kWarps, num_sms);
+}
+
+template <typename T>
+static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
+{
     PcgDesc<T> &h = run.h;
-    h.tiles_x = (h.nth + TX - 1) / TX;
-    h.tiles_y = (h.nz + TY - 1) / TY;
+    run.ks = ks;
+    h.tiles_x = (h.nth + ks.W - 1) / ks.W;
+    h.tiles_y = (h.nz + ks.TY - 1) / ks.TY;
     h.ntiles = (long long)h.tiles_x * h.tiles_y * h.K;
-    run.grid_a = grid_for((const void *)k_phase_a<T, TX, TY>, h.ntiles, ctx->num_sms);
-    run.grid_b = grid_for((const void *)k_phase_b<T, TX, TY, false>, h.ntiles, ctx->num_sms);
+    run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms);
+    run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms);
     run.grid_s = stream_grid(h.n * h.K, ctx->num_sms);
-    int gm = run.grid_a > run.grid_b ? run.grid_a : run.grid_b;
-    if (run.grid_s > gm) gm = run.grid_s;
-    GMAF_TRY(ensure(ctx, B_PART, (size_t)2 * gm * sizeof(double)));
-    h.partials = (double *)ctx->buf[B_PART];
-    run.d_desc = desc_slot;
+}
+
+template <typename T>
+static size_t partial_doubles(const PcgRun<T> &run)
+{
+    long long m = 2 * run.h.ntiles;
+    if (2LL * run.grid_s > m) m = 2LL * run.grid_s;
+    return (size_t)m;
+}
+
+// Autotuner: time one iteration (phase A + phase B) of every candidate on the
+// run's own data and keep the fastest for this shape.  The tuning iterate
+// lives in run.h.p, which the real solve zero-initialises afterwards.
+template <typename T>
+static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand, int *best_out)
+{
+    cudaStream_t s = ctx->stream;
+    if (!ctx->ev_ready) {
+        for (auto &ev : ctx->ev) GMAF_CUDA(cudaEventCreate(&ev));
+        ctx->ev_ready = 1;
+    }
+    PcgRun<T> tr = run;
+    tr.h.zero_init = 1;
+    tr.h.eps = 1e-300;          // never converges during tuning
+    tr.h.max_iter = 1 << 30;
+    tr.h.use_cond = 0;
+    float best = 3.0e38f;
+    int best_i = 0;
+    for (int c = 0; c < ncand; ++c) {
+        shape_run<T>(ctx, tr, cand[c]);
+        GMAF_TRY(ensure(ctx, B_PART, partial_doubles(tr) * sizeof(double)));
+        tr.h.partials = (double *)ctx->buf[B_PART];
+        GMAF_CUDA(cudaMemcpyAsync(tr.d_desc, &tr.h, sizeof(PcgDesc<T>), cudaMemcpyHostToDevice, s));
+        k_reset<<<1, 32, 0, s>>>(tr.h.sc, 0);
+        k_init_r<T><<<tr.grid_s, kThreads, 0, s>>>(tr.d_desc);
+        GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s));
+        const int warm = 3, reps = 10;
+        for (int q = 0; q < warm + reps; ++q) {
+            if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
+            GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s));
+            GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s));
+        }
+        GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
+        GMAF_CUDA(cudaEventSynchronize(ctx->ev[1]));
+        float ms = 0.0f;
+        GMAF_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        if (ms < best) {
+            best = ms;
+            best_i = c;
+        }
+    }
+    *best_out = best_i;
     return GMAF_OK;
 }
 
-// Upload the descriptor, building the loop graph first when needed.
+// Kernel set (tuned per shape), launch shape, partial-sum buffer and
+// descriptor slot of a run.
+template <typename T>
+static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
+{
+    PcgDesc<T> &h = run.h;
+    run.d_desc = desc_slot;
+    KernelSet<T> cand[kMaxVariants];
+    const bool vo = vec_ok(h);
+    const int ncand = variants(cand, vo);
+    int pick = 0;
+    TuneEntry key{};
+    key.tsize = (int)sizeof(T);
+    key.nth = h.nth;
+    key.nz = h.nz;
+    key.K = h.K;
+    key.precond = h.precond;
+    key.vec_ok = vo ? 1 : 0;
+    int found = -1;
+    for (int q = 0; q < ctx->ntune; ++q) {
+        const TuneEntry &e = ctx->tune[q];
+        if (e.tsize == key.tsize && e.nth == key.nth && e.nz == key.nz && e.K == key.K &&
+            e.precond == key.precond && e.vec_ok == key.vec_ok)
+            found = q;
+    }
+    int forced = -1;
+    for (int q = 0; q < ncand; ++q)
+        if (cand[q].id == ctx->force_variant) forced = q;
+    if (forced >= 0) {
+        pick = forced;
+    } else if (found >= 0) {
+        pick = ctx->tune[found].choice;
+    } else if (!ctx->no_tune && ncand > 1 && h.zero_init) {
+        GMAF_TRY(autotune<T>(ctx, run, cand, ncand, &pick));
+        key.choice = pick;
+        const int slot = ctx->ntune < kTuneEntries ? ctx->ntune++ : (ctx->tune_next++ % kTuneEntries);
+        ctx->tune[slot] = key;
+    }
+    if (pick < 0 || pick >= ncand) pick = 0;
+    shape_run<T>(ctx, run, cand[pick]);
+    GMAF_TRY(ensure(ctx, B_PART, partial_doubles(run) * sizeof(double)));
+    h.partials = (double *)ctx->buf[B_PART];
+    return GMAF_OK;
+}
+
 // The loop runs as a graph WHILE node unless the host drives it in chunks
 // (GMAF_NO_GRAPH, or per-phase event timing).  Only kernels launched by that
 // graph may write its condition, so the descriptor enables the condition
@@ -710,7 +1193,7 @@ static int prepare(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc)
     if (!use_graph(ctx)) {
         run.h.use_cond = 0;
     } else {
-        if (!graph_matches(gc, run.grid_a, run.grid_b, run.grid_s, run.d_desc))
+        if (!graph_matches(gc, run.grid_a, run.grid_b, run.grid_s, run.d_desc, run.ks.a))
             GMAF_TRY(build_graph<T>(run, gc, ctx->stream));
         run.h.use_cond = 1;
         run.h.cond = gc.handle;
@@ -767,14 +1250,12 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
     }
     if (run.h.use_cond) return GMAF_CUDA_ERROR;
     // host-chunked loop control: phases return at once after `done` is set
-    constexpr int TX = TileCfg<T>::TX, TY = TileCfg<T>::TY;
     const PcgDesc<T> *dd = run.d_desc;
     int *done_h = (int *)ctx->pinned;
     PhaseClock clk{ctx};
     clk.begin(s);
-    k_phase_b<T, TX, TY, true><<<run.grid_b, kThreads, 0, s>>>(dd);
+    GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s));
     clk.end(s, 2);
-    GMAF_CUDA(cudaGetLastError());
     const int chunk = 16;
     for (int it = 0; it <= run.h.max_iter + chunk; it += chunk) {
         GMAF_CUDA(cudaMemcpyAsync(done_h, &run.h.sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -783,13 +1264,12 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
         if (*done_h) break;
         for (int q = 0; q < chunk; ++q) {
             clk.begin(s);
-            k_phase_a<T, TX, TY><<<run.grid_a, kThreads, 0, s>>>(dd);
+            GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s));
             clk.end(s, 0);
             clk.begin(s);
-            k_phase_b<T, TX, TY, false><<<run.grid_b, kThreads, 0, s>>>(dd);
+            GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s));
             clk.end(s, 1);
         }
-        GMAF_CUDA(cudaGetLastError());
     }
     k_finalize<T><<<run.grid_s, kThreads, 0, s>>>(dd);
     return cuda_status(cudaGetLastError());
@@ -906,6 +1386,8 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
             inf.true_rel_residual = true_rel;
             inf.restarts = restarted;
             inf.outer_iterations = 1;
+            inf.kernel_variant = run.ks.id;
+            inf.tasks = (int)run.h.ntiles;
             if (hsc->status != 0 || ho->status != 0) {
                 inf.status = hsc->status != 0 ? hsc->status : ho->status;
                 break;
@@ -964,8 +1446,10 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     h.omega = (float)opts->omega;
     h.c1 = (float)(opts->omega * (2.0 - opts->omega));
     h.sc = dsc;
-    GMAF_TRY(setup_run<float>(ctx, run, (PcgDesc<float> *)(dbase + 1024)));
-    rd.partials = h.partials;
+    // The first outer residual and the inner right-hand side are formed before the
+    // kernel set is chosen, so that the autotuner times iterations on real data.
+    GMAF_TRY(ensure(ctx, B_PART, (size_t)2 * gs * sizeof(double)));
+    rd.partials = (double *)ctx->buf[B_PART];
     rd.sc = dsc_outer;
     rd.r = (double *)ctx->buf[B_R64];
     GMAF_CUDA(cudaMemcpyAsync(d_rdesc, &rd, sizeof(ResidDesc), cudaMemcpyHostToDevice, s));
@@ -973,6 +1457,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     const double inner_floor = 1e-5;
     const int max_outer = 12;
     int total_inner = 0, outer = 0;
+    bool tuned = false;
     inf.status = GMAF_NOT_CONVERGED;
     for (;;) {
         {
@@ -995,6 +1480,15 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
             break;
         }
         if (outer >= max_outer || total_inner >= opts->max_iter) break;
+        k_make_b32<<<gs, kThreads, 0, s>>>((const double *)ctx->buf[B_R64], (float *)ctx->buf[B_B32],
+                                           N, dsc_outer);
+        GMAF_CUDA(cudaGetLastError());
+        if (!tuned) {
+            GMAF_TRY(setup_run<float>(ctx, run, (PcgDesc<float> *)(dbase + 1024)));
+            rd.partials = h.partials;
+            GMAF_CUDA(cudaMemcpyAsync(d_rdesc, &rd, sizeof(ResidDesc), cudaMemcpyHostToDevice, s));
+            tuned = true;
+        }
         // inner tolerance: a fixed reduction, but no further than the outer target needs
         double eps_in = 0.5 * opts->eps / ho->true_rel;
         if (eps_in < inner_floor) eps_in = inner_floor;
@@ -1002,9 +1496,6 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         h.eps = eps_in;
         h.max_iter = opts->max_iter - total_inner;
         GMAF_TRY(prepare<float>(ctx, run, ctx->graph32));
-        k_make_b32<<<gs, kThreads, 0, s>>>((const double *)ctx->buf[B_R64], (float *)ctx->buf[B_B32],
-                                           N, dsc_outer);
-        GMAF_CUDA(cudaGetLastError());
         GMAF_TRY(pcg_once<float>(ctx, run, ctx->graph32, false, true));
         k_update_p64<<<gs, kThreads, 0, s>>>(p, (const float *)ctx->buf[B_X32], N, dsc_outer);
         GMAF_CUDA(cudaGetLastError());
@@ -1019,6 +1510,8 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     }
     inf.iterations = total_inner;
     inf.outer_iterations = outer;
+    inf.kernel_variant = run.ks.id;
+    inf.tasks = (int)run.h.ntiles;
     *info = inf;
     return inf.status;
 }
@@ -1045,9 +1538,9 @@ constexpr size_t kNaDesc = 0;          // PcgDesc<double>
 constexpr size_t kNaResid = 2048;      // ResidDesc
 constexpr size_t kNaScal = 4096;       // Scalars of the run, Scalars of the residual
 constexpr size_t kNaCslot = 8192;      // int[kMaxCond], identity coefficient map
-constexpr size_t kNaPart = 16384;      // block partial sums
-constexpr size_t kNaPartBytes = 65536;
-constexpr size_t kNaVec = 131072;      // 1/D, r0, r1, u0, u1, z, v: N doubles each
+constexpr size_t kNaPart = 16384;      // per-task / per-block partial sums
+constexpr size_t kNaPartBytes = 524288;
+constexpr size_t kNaVec = 1048576;     // 1/D, r0, r1, u0, u1, z, v: N doubles each
 constexpr int kNaMaxDevices = 64;
 static_assert(sizeof(PcgDesc<double>) <= kNaResid - kNaDesc, "descriptor slot");
 static_assert(sizeof(ResidDesc) <= kNaScal - kNaResid, "residual descriptor slot");
@@ -1105,24 +1598,14 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     if (e != cudaSuccess) return cuda_status(e);
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    constexpr int TX = TileCfg<double>::TX, TY = TileCfg<double>::TY;
     PcgDesc<double> h{};
     h.nth = nth;
     h.nz = nz;
     h.K = K;
     h.n = n;
-    h.tiles_x = (nth + TX - 1) / TX;
-    h.tiles_y = (nz + TY - 1) / TY;
-    h.ntiles = (long long)h.tiles_x * h.tiles_y * K;
     h.precond = opts->precond;
     h.zero_init = opts->zero_init;
     h.use_cond = 0;
-    const int grid_a = grid_for((const void *)k_phase_a<double, TX, TY>, h.ntiles, num_sms);
-    const int grid_b = grid_for((const void *)k_phase_b<double, TX, TY, false>, h.ntiles, num_sms);
-    const int grid_s = stream_grid(N, num_sms);
-    int gm = grid_a > grid_b ? grid_a : grid_b;
-    if (grid_s > gm) gm = grid_s;
-    if ((size_t)2 * gm * sizeof(double) > kNaPartBytes) return GMAF_OUT_OF_MEMORY;
     double *vbase = (double *)(base + kNaVec);
     double *invD = vbase;
     double *vecs[6];
@@ -1149,6 +1632,16 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     h.max_iter = opts->max_iter;
     h.sc = dsc;
     h.partials = (double *)(base + kNaPart);
+    const KernelSet<double> ks = choose_kernels<double>(h);
+    h.tiles_x = (nth + ks.W - 1) / ks.W;
+    h.tiles_y = (nz + ks.TY - 1) / ks.TY;
+    h.ntiles = (long long)h.tiles_x * h.tiles_y * K;
+    const int grid_a = phase_grid(ks.a, h.ntiles, num_sms);
+    const int grid_b = phase_grid(ks.b, h.ntiles, num_sms);
+    const int grid_s = stream_grid(N, num_sms);
+    long long np = 2 * h.ntiles;
+    if (2LL * grid_s > np) np = 2LL * grid_s;
+    if ((size_t)np * sizeof(double) > kNaPartBytes) return GMAF_OUT_OF_MEMORY;
     PcgDesc<double> *d_desc = (PcgDesc<double> *)(base + kNaDesc);
     ResidDesc *d_rdesc = (ResidDesc *)(base + kNaResid);
     ResidDesc rd{};
@@ -1186,8 +1679,8 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     for (;;) {
         k_reset<<<1, 32, 0, s>>>(dsc, keep ? 1 : 0);
         if (init_r) k_init_r<double><<<grid_s, kThreads, 0, s>>>(d_desc);
-        k_phase_b<double, TX, TY, true><<<grid_b, kThreads, 0, s>>>(d_desc);
-        e = cudaGetLastError();
+        e = launch<double>(ks.b_init, grid_b, d_desc, s);
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
         const int chunk = 16;
         for (int it = 0; it <= opts->max_iter + chunk; it += chunk) {
@@ -1196,11 +1689,10 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_status(e);
             if (done) break;
-            for (int q = 0; q < chunk; ++q) {
-                k_phase_a<double, TX, TY><<<grid_a, kThreads, 0, s>>>(d_desc);
-                k_phase_b<double, TX, TY, false><<<grid_b, kThreads, 0, s>>>(d_desc);
+            for (int q = 0; q < chunk && e == cudaSuccess; ++q) {
+                e = launch<double>(ks.a, grid_a, d_desc, s);
+                if (e == cudaSuccess) e = launch<double>(ks.b, grid_b, d_desc, s);
             }
-            e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_status(e);
         }
         k_finalize<double><<<grid_s, kThreads, 0, s>>>(d_desc);

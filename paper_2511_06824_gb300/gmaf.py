@@ -61,7 +61,8 @@ class gmaf_solver_opts(ctypes.Structure):
 class gmaf_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
                 ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
+                ("kernel_variant", ctypes.c_int32), ("tasks", ctypes.c_int32)]
 
 
 class GmafError(RuntimeError):

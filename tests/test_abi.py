@@ -67,6 +67,7 @@ int main(void) {
   P(gmaf_solver_opts, omega) P(gmaf_solver_opts, eps) P(gmaf_solver_opts, max_iter)
   P(gmaf_solver_opts, precision) P(gmaf_solver_opts, zero_init)
   P(gmaf_solve_info, rel_residual) P(gmaf_solve_info, true_rel_residual)
+  P(gmaf_solve_info, kernel_variant) P(gmaf_solve_info, tasks)
   P(gmaf_physics, p_case)
   return 0;
 }
