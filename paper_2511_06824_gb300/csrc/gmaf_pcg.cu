@@ -373,19 +373,35 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
         const int hslot = lane == 0 ? 3 : W + 4;
 
         auto load_row = [&](int jr, RowA<T, VEC> &R) {
+            if (jr < 0 || jr >= nz) {
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) R.z[q] = R.uo[q] = R.D[q] = R.e[q] = R.n[q] = R.p[q] = T(0);
-            R.hz = R.huo = R.he = T(0);
-            if (jr < 0 || jr >= nz) return;
+                for (int q = 0; q < VEC; ++q) R.z[q] = R.uo[q] = R.D[q] = R.e[q] = R.n[q] = R.p[q] = T(0);
+                R.hz = R.huo = R.he = T(0);
+                return;
+            }
             const size_t q0 = (size_t)jr * nth + g0;
             Vec<T, VEC>::ld(z + q0, R.z);
-            if (!first) Vec<T, VEC>::ld(uo + q0, R.uo);
+            if (!first) {
+                Vec<T, VEC>::ld(uo + q0, R.uo);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.uo[q] = T(0);
+            }
             Vec<T, VEC>::ld(aN + q0, R.n);
             if (jr >= tk.j0 && jr < tk.jend) {
                 Vec<T, VEC>::ld(D + q0, R.D);
                 Vec<T, VEC>::ld(aE + q0, R.e);
-                if (!first && owned) Vec<T, VEC>::ldrw(pp + q0, R.p);
+                if (!first && owned) {
+                    Vec<T, VEC>::ldrw(pp + q0, R.p);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) R.p[q] = T(0);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.D[q] = R.e[q] = R.p[q] = T(0);
             }
+            R.hz = R.huo = R.he = T(0);
             if (lane < 2) {
                 const size_t qh = (size_t)jr * nth + hg;
                 R.hz = __ldg(z + qh);
@@ -543,13 +559,20 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__
         const int hslot = lane < 2 ? lane + 2 : W + 2 + lane;
 
         auto load_row = [&](int jr, RowB<T, VEC> &R) {
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) R.r[q] = R.v[q] = R.dI[q] = R.e[q] = R.n[q] = T(0);
             R.hr = R.hv = R.hd = R.he = R.hn = T(0);
-            if (jr < 0 || jr >= nz) return;
+            if (jr < 0 || jr >= nz) {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.r[q] = R.v[q] = R.dI[q] = R.e[q] = R.n[q] = T(0);
+                return;
+            }
             const size_t q0 = (size_t)jr * nth + g0;
             Vec<T, VEC>::ld(ro + q0, R.r);
-            if (!INIT) Vec<T, VEC>::ld(vv + q0, R.v);
+            if (!INIT) {
+                Vec<T, VEC>::ld(vv + q0, R.v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.v[q] = T(0);
+            }
             Vec<T, VEC>::ld(invD + q0, R.dI);
             Vec<T, VEC>::ld(aE + q0, R.e);
             Vec<T, VEC>::ld(aN + q0, R.n);
@@ -1107,31 +1130,35 @@ static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand
     tr.h.eps = 1e-300;          // never converges during tuning
     tr.h.max_iter = 1 << 30;
     tr.h.use_cond = 0;
-    float best = 3.0e38f;
-    int best_i = 0;
-    for (int c = 0; c < ncand; ++c) {
-        shape_run<T>(ctx, tr, cand[c]);
-        GMAF_TRY(ensure(ctx, B_PART, partial_doubles(tr) * sizeof(double)));
-        tr.h.partials = (double *)ctx->buf[B_PART];
-        GMAF_CUDA(cudaMemcpyAsync(tr.d_desc, &tr.h, sizeof(PcgDesc<T>), cudaMemcpyHostToDevice, s));
-        k_reset<<<1, 32, 0, s>>>(tr.h.sc, 0);
-        k_init_r<T><<<tr.grid_s, kThreads, 0, s>>>(tr.d_desc);
-        GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s));
-        const int warm = 3, reps = 10;
-        for (int q = 0; q < warm + reps; ++q) {
-            if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
-            GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s));
-            GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s));
-        }
-        GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
-        GMAF_CUDA(cudaEventSynchronize(ctx->ev[1]));
-        float ms = 0.0f;
-        GMAF_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
-        if (ms < best) {
-            best = ms;
-            best_i = c;
+    // two round-robin passes, best time per candidate: the first pass also
+    // brings the clocks up and loads every kernel
+    float best_t[kMaxVariants];
+    for (int c = 0; c < ncand; ++c) best_t[c] = 3.0e38f;
+    for (int round = 0; round < 2; ++round) {
+        for (int c = 0; c < ncand; ++c) {
+            shape_run<T>(ctx, tr, cand[c]);
+            GMAF_TRY(ensure(ctx, B_PART, partial_doubles(tr) * sizeof(double)));
+            tr.h.partials = (double *)ctx->buf[B_PART];
+            GMAF_CUDA(cudaMemcpyAsync(tr.d_desc, &tr.h, sizeof(PcgDesc<T>), cudaMemcpyHostToDevice, s));
+            k_reset<<<1, 32, 0, s>>>(tr.h.sc, 0);
+            k_init_r<T><<<tr.grid_s, kThreads, 0, s>>>(tr.d_desc);
+            GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s));
+            const int warm = 3, reps = 10;
+            for (int q = 0; q < warm + reps; ++q) {
+                if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
+                GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s));
+                GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s));
+            }
+            GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
+            GMAF_CUDA(cudaEventSynchronize(ctx->ev[1]));
+            float ms = 0.0f;
+            GMAF_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+            if (ms < best_t[c]) best_t[c] = ms;
         }
     }
+    int best_i = 0;
+    for (int c = 1; c < ncand; ++c)
+        if (best_t[c] < best_t[best_i]) best_i = c;
     *best_out = best_i;
     return GMAF_OK;
 }
