@@ -169,8 +169,11 @@ int gmaf_integrate_loads(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physic
  *   G = (Fx - My/L, Fy + Mx/L, My/L, -Mx/L) + F_ext
  * and the update of (e, edot) from (J_edot + dt J_e) delta = -G - J_e (e_prev
  * + dt edot - e), edot += delta, e = e_prev + dt edot.
- * All arguments are host memory.  state is updated in place only when the
- * solve converged.  loads_out[12]: loads of the base condition; J_out[48]:
+ * All arguments are host memory.  opts->zero_init = 1 starts the joint solve
+ * from p = 0 (Table 1 step 1); 0 starts it from the 9 pressure fields the
+ * previous gmaf_picard_step call on this context left behind when that call
+ * had the same grid (the usual case inside a Picard loop or a time march),
+ * else from 0.  state is updated in place only when the solve converged.  loads_out[12]: loads of the base condition; J_out[48]:
  * row-major 6 x 8 Jacobian (columns e1..e4, edot1..edot4); G_out[4]: G before
  * the update.  Synchronises the stream. */
 int gmaf_picard_step(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *phys,

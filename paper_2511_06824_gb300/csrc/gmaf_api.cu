@@ -332,10 +332,15 @@ int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phy
     if ((st = launch_assemble(g, K, conds, cslot_write, D, aE, aN, S, (const double *)c->buf[B_TRIG],
                               (int *)c->buf[B_FLAGS], NSLOT, s)))
         return st;
-    // (a3) joint solve; conditions 5..8 (edot perturbations) use the coefficients of condition 0
+    // (a3) joint solve; conditions 5..8 (edot perturbations) use the coefficients of condition 0.
+    // zero_init = 0 warm-starts from the fields the previous step of this shape left in
+    // the context (the previous Picard iterate or time step); otherwise from zero.
     const int cslot[9] = {0, 1, 2, 3, 4, 0, 0, 0, 0};
     gmaf_solver_opts o = *opts;
-    o.zero_init = 1;
+    const bool warm = !opts->zero_init && c->pp_nth == g.nth && c->pp_nz == g.nz;
+    o.zero_init = warm ? 0 : 1;
+    c->pp_nth = g.nth;
+    c->pp_nz = g.nz;
     gmaf_solve_info info{};
     const int sst = solve_joint_device(c, g.nth, g.nz, K, NSLOT, cslot, D, aE, aN, S, p, &o, &info);
     c->info = info;

@@ -130,6 +130,7 @@ struct gmaf_ctx {
     int force_variant;             // GMAF_VARIANT=<id>: use that kernel variant when eligible
     gmaf::TuneEntry tune[gmaf::kTuneEntries];
     int ntune, tune_next;
+    int pp_nth, pp_nz;             // shape of the Picard-step fields held in B_PP
 };
 
 namespace gmaf {

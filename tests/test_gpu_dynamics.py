@@ -1,0 +1,88 @@
+"""Multi-period march (shaft-angle steps of Picard iterations) on the GPU against
+the same march written with the oracle's Picard step."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_06824_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_06824_gb300 import build, gmaf
+    build.build()
+    gmaf.load()
+    return gmaf
+
+
+def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, max_picard=20):
+    dt = (60.0 / 600.0) / 360.0
+    out = []
+    for s in range(steps):
+        phi = 2 * math.pi * (s % 360) / 360
+        ph = phys.copy()
+        ph[5] = prof[s % 360]
+        ph[4] = 5.0 * math.sin(phi)
+        f = kappa * ph[5] * math.pi * ph[0] ** 2 * math.tan(math.radians(10.0))
+        F = np.array([0.0, 0.0, f, 0.0])
+        e_prev = st[:4].copy()
+        for _ in range(max_picard):
+            r = oracle.picard_step(nth, nz, ph, tex, st, e_prev, dt, F, 2e-8, 1e-6, eps=eps)
+            assert r["status"] == 0
+            if np.linalg.norm(r["G"]) <= tol_F * max(np.linalg.norm(F), 1.0):
+                break
+            st = r["state"]
+        out.append(st.copy())
+    return np.array(out)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-6), (1, 1e-4)])
+def test_march_matches_oracle(g, precision, tol):
+    from paper_2511_06824_gb300 import dynamics
+    nth, nz, steps = 48, 24, 10
+    phys = inputs.phys_vector()
+    tex = inputs.dimple_texture(np.random.default_rng(4))
+    prof = inputs.trapezoid_pressure_profile(np.random.default_rng(3), 360)
+    st0 = np.array([2e-6, -1e-6, 3e-6, 1e-6, 0, 0, 0, 0.0])
+    eps = 1e-12
+    with g.Context() as c:
+        traj = dynamics.march(c.handle, nth, nz, phys, tex, st0, prof, steps, kappa=0.2,
+                              opts=g.solver_opts(eps=eps, precision=precision))
+    ref = oracle_march(nth, nz, phys, tex, st0.copy(), prof, steps, 0.2, eps)
+    got = traj.states
+    assert all(r.converged for r in traj.records)
+    scale = np.abs(ref[:, :4]).max()
+    assert np.max(np.abs(got[:, :4] - ref[:, :4])) <= tol * scale
+    rscale = np.abs(ref[:, 4:]).max()
+    assert np.max(np.abs(got[:, 4:] - ref[:, 4:])) <= 10 * tol * rscale
+
+
+def test_warm_start_saves_iterations_and_keeps_the_answer(g):
+    """zero_init = 0 starts from the fields the previous step of this context left:
+    re-solving at the same state needs almost no iterations and gives the same loads."""
+    w = inputs.make("textured-128x64-k9", 2)
+    dt = 2.78e-4
+    F = np.array([30.0, -10.0, 5.0, 1.0])
+    with g.Context() as c:
+        cold = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state, w.state[:4],
+                                  dt, F, w.d_e, w.d_edot, g.solver_opts(eps=1e-12))
+        warm = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state, w.state[:4],
+                                  dt, F, w.d_e, w.d_edot, g.solver_opts(eps=1e-12, zero_init=0))
+        # a different shape in between invalidates the stored fields: back to a cold start
+        g.gmaf_picard_step(c.handle, 64, 32, w.phys, w.tex, w.state, w.state[:4], dt, F, w.d_e,
+                           w.d_edot, g.solver_opts(eps=1e-12))
+        again = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state,
+                                   w.state[:4], dt, F, w.d_e, w.d_edot,
+                                   g.solver_opts(eps=1e-12, zero_init=0))
+    assert warm["iters"] <= 0.2 * cold["iters"]
+    assert again["iters"] == cold["iters"]
+    scale = np.maximum(np.abs(cold["loads"]), 1e-3 * np.linalg.norm(cold["loads"]))
+    assert np.max(np.abs(warm["loads"] - cold["loads"]) / scale) < 1e-8
+    np.testing.assert_allclose(warm["state"], cold["state"], rtol=1e-6, atol=1e-14)
