@@ -58,9 +58,13 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "dynamics"], default="step",
+    ap.add_argument("--mode", choices=["step", "dynamics", "serving"], default="step",
                     help="step: Picard steps of the joint batch (default); dynamics: the "
-                         "multi-period march on the textured 1024x512 gap")
+                         "multi-period march on the textured 1024x512 gap; serving: a Poisson "
+                         "stream of uneven requests, batched server vs sequential FP64")
+    ap.add_argument("--requests", type=int, default=24, help="requests in the stream (serving)")
+    ap.add_argument("--rate", type=float, default=20.0, help="arrival rate [1/s] (serving)")
+    ap.add_argument("--budget-gb", type=float, default=24.0, help="server HBM budget (serving)")
     ap.add_argument("--dyn-steps", type=int, default=36, help="shaft-angle steps (dynamics)")
     return ap.parse_args()
 
@@ -467,12 +471,52 @@ def run_dynamics(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args):
+    """Poisson stream of Picard-step requests, grids uniform over 256x128 .. 2048x1024,
+    half of them textured: the continuous-batching mixed-precision server against the
+    sequential one-system-at-a-time FP64 baseline, same requests, same tolerance."""
+    import torch
+    from paper_2511_06824_gb300 import build as gbuild
+    from paper_2511_06824_gb300 import gmaf, inputs, serving
+    gbuild.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = inputs.serving_requests(seed=args.seed, count=args.requests, rate_hz=args.rate)
+    items = serving.items_from_requests(reqs)
+    eps = 1e-10
+    with gmaf.Context() as c:
+        warm = serving.items_from_requests(inputs.serving_requests(seed=999, count=2, rate_hz=1e6,
+                                                                   grids=[(256, 128)]))
+        serving.serve_stream(c.handle, warm, 2 << 30, eps=eps)          # load kernels
+        serving.sequential_stream(c.handle, warm[:1], eps=eps)
+        budget = int(args.budget_gb * (1 << 30))
+        sv = serving.serve_stream(c.handle, items, budget, eps=eps, round_iters=64)
+        sq = serving.sequential_stream(c.handle, items, eps=eps)
+    err = max(serving.load_error(a["loads"], b["loads"]) for a, b in zip(sv["results"], sq["results"]))
+    dof = sum(9 * r["n_theta"] * r["n_z"] for r in reqs)
+    out = {"metric": "Picard steps/s (served stream) and p50/p99 step latency",
+           "value": sv["picard_steps_per_s"], "unit": "Picard steps/s", "higher_is_better": True,
+           "n_gpus": 1, "data": "synthetic", "dtype": "f32+f64",
+           "served": {k: sv[k] for k in ("picard_steps_per_s", "p50_ms", "p99_ms", "mean_ms",
+                                         "span_s", "max_active")},
+           "sequential_fp64": {k: sq[k] for k in ("picard_steps_per_s", "p50_ms", "p99_ms",
+                                                  "mean_ms", "span_s")},
+           "speedup_steps_per_s": sv["picard_steps_per_s"] / sq["picard_steps_per_s"],
+           "max_load_difference_served_vs_sequential": err,
+           "config": {"workload": "poisson-stream", "requests": args.requests,
+                      "rate_hz": args.rate, "grids": [list(x) for x in inputs.SERVING_GRIDS],
+                      "textured_fraction": 0.5, "eps": eps, "budget_gb": args.budget_gb,
+                      "total_joint_dof": dof, "round_iters": 64}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "dynamics":
         run_dynamics(args)
+    elif args.mode == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -218,6 +218,62 @@ int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, const double
                              const gmaf_solver_opts *opts, void *cuda_stream, int32_t *iters_out,
                              double *rel_res_out);
 
+/* ---- continuous-batching server (the benchmark spec serving pattern) ----------
+ * Requests are single Picard iterations (as gmaf_picard_step, always in the
+ * mixed-precision mode, ASSOR-II) of a 9-condition joint batch on their own
+ * grid (n_theta must be a multiple of 4).  gmaf_server_submit queues a request;
+ * gmaf_server_run admits queued requests first-come first-served while their
+ * device footprint (gmaf_request_footprint) fits in the server's arena of
+ * hbm_budget_bytes (allocated once at creation on the context's device and
+ * stream), advances all admitted requests together by `iterations` batched PCG
+ * iterations (one persistent kernel per CG phase over every request's tasks),
+ * then takes the FP64 refinement step of every request whose inner solve ended
+ * and either restarts it or finishes it (loads, Jacobian, update) and frees its
+ * memory.  Finished results are collected with gmaf_server_poll in completion
+ * order.  Each request keeps its own scalars and convergence test
+ * (Eq. 3.9 per request), so its result does not depend on which other
+ * requests share the GPU.  Not thread-safe. */
+typedef struct gmaf_server gmaf_server;
+
+typedef struct {
+    gmaf_grid grid;
+    gmaf_physics phys;
+    gmaf_texture tex;
+    gmaf_state state;          /* state at which the step is evaluated */
+    double e_prev[4];          /* eccentricity at the previous time point */
+    double dt;
+    double F_ext[4];           /* generalized external force */
+    double d_e, d_edot;        /* forward-difference steps */
+    double omega, eps;         /* ASSOR relaxation, Eq. 3.9 tolerance (FP64 residual) */
+    int32_t max_iter;          /* inner PCG iteration budget */
+} gmaf_request;
+
+typedef struct {
+    int64_t id;
+    int32_t status;            /* GMAF_OK, GMAF_NOT_CONVERGED, GMAF_CONTACT, ... */
+    int32_t iterations;        /* inner PCG iterations */
+    int32_t outer_iterations;  /* refinement sweeps */
+    double true_rel_residual;
+    gmaf_state state;          /* updated state (input state unless GMAF_OK) */
+    double loads[12];          /* base-condition loads: pressure then shear */
+    double J[48];              /* 6 x 8 Jacobian, row-major */
+    double G[4];               /* generalized force before the update */
+} gmaf_result;
+
+/* Device bytes one request of this grid occupies in a server's arena. */
+int gmaf_request_footprint(const gmaf_grid *grid, size_t *bytes_out);
+int gmaf_server_create(gmaf_ctx *ctx, size_t hbm_budget_bytes, gmaf_server **out);
+int gmaf_server_destroy(gmaf_server *server);
+/* Queue a request; *id_out receives its id.  GMAF_OUT_OF_MEMORY if it can never fit. */
+int gmaf_server_submit(gmaf_server *server, const gmaf_request *request, int64_t *id_out);
+/* Admit, advance by `iterations` batched PCG iterations, refine/finish; synchronises. */
+int gmaf_server_run(gmaf_server *server, int32_t iterations, int32_t *active_out,
+                    int32_t *queued_out);
+/* Move up to max_results finished results to out; *n_out receives the count. */
+int gmaf_server_poll(gmaf_server *server, gmaf_result *out, int32_t max_results, int32_t *n_out);
+/* Free bytes left in the server's arena. */
+int gmaf_server_free_bytes(const gmaf_server *server, size_t *bytes_out);
+
 /* Static description of a status code. */
 const char *gmaf_status_string(int status);
 

@@ -1,0 +1,1095 @@
+// Device code of the joint PCG: accumulation, reductions, the strip-marching
+// phase kernels (single joint system and batched groups), initialisation,
+// residual and mixed-precision glue kernels.  Included by gmaf_pcg.cu (solver
+// driver) and gmaf_server.cu (batched serving).
+//
+// Table 1 (with r0 = S - A p0) on the block-diagonal joint system of Eq. 3.7-3.8,
+// one set of scalars per joint system and the synchronized criterion of Eq. 3.9;
+// preconditioner ASSOR-II (Eq. 3.3-3.6) or Jacobi (Eq. 2.8).
+#pragma once
+
+#include <cmath>
+
+#include "gmaf_internal.cuh"
+
+namespace gmaf {
+
+// ------------------------------------------------------------------ accumulation
+
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// Two-float accumulation: exact products (TwoProduct with an FMA) and
+// compensated sums (TwoSum), so a thread's partial is accurate to about 2^-44
+// relative to the sum of magnitudes before it is handed to FP64.
+template <>
+struct Acc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ double warp_sum_d(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block-reduce NV values, publish the block partial, and let the last block
+// (by ticket) form the totals in block order.  Returns true in the last block;
+// tot[] is valid in thread 0 of that block.
+template <int NV>
+__device__ __forceinline__ bool reduce_last(const double (&val)[NV], double *partials,
+                                            unsigned int *ticket, double (&tot)[NV])
+{
+    __shared__ double red[NV][32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const double s = warp_sum_d(val[q]);
+        if (lane == 0) red[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[q][w];
+            partials[(size_t)q * gridDim.x + blockIdx.x] = s;
+        }
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            s += __ldcg(&partials[(size_t)q * gridDim.x + b]);
+        s = warp_sum_d(s);
+        __syncthreads();
+        if (lane == 0) red[q][wid] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[q][w];
+            tot[q] = t;
+        }
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+// ------------------------------------------------------------------ strip-marching tiles
+//
+// A task is one condition x one strip of W = 32 * VEC consecutive columns x TY
+// rows.  One warp owns a task: lane l holds columns i0 + l*VEC .. +VEC-1 (one
+// 16-byte vector per field and row) and the warp marches down the rows keeping
+// the rows above and below in registers; the theta neighbours of a row go
+// through a one-row shared buffer of the warp (slot s <-> column i0 - 2 + s in
+// phase B, i0 - 1 + s in phase A) filled by the owners and, for the halo
+// columns, by lanes 0..3.  Column indices are reduced modulo n_theta once per
+// task, so the periodic wrap costs nothing per cell; lanes whose columns lie
+// beyond n_theta compute the wrapped columns (their values are neighbours of the
+// owned ones) but store nothing.  Requires n_theta % VEC == 0 and 16-byte
+// aligned arrays for VEC > 1.
+//
+// Tasks are numbered with the condition fastest, so the warps working on one
+// spatial strip at the same time read a shared coefficient slot once from DRAM.
+
+constexpr int kWarps = kThreads / 32;
+
+template <typename T, int VEC>
+struct Vec;
+template <typename T>
+struct Vec<T, 1> {
+    static __device__ __forceinline__ void ld(const T *p, T (&x)[1]) { x[0] = __ldg(p); }
+    static __device__ __forceinline__ void ldrw(const T *p, T (&x)[1]) { x[0] = *p; }
+    static __device__ __forceinline__ void st(T *p, const T (&x)[1]) { *p = x[0]; }
+};
+template <>
+struct Vec<float, 4> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[4])
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    }
+    static __device__ __forceinline__ void ldrw(const float *p, float (&x)[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+template <>
+struct Vec<float, 2> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[2])
+    {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void ldrw(const float *p, float (&x)[2])
+    {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[2])
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    }
+};
+template <>
+struct Vec<double, 2> {
+    static __device__ __forceinline__ void ld(const double *p, double (&x)[2])
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void ldrw(const double *p, double (&x)[2])
+    {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&x)[2])
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
+    }
+};
+
+// Dot-product accumulation: a row's VEC products are summed in T, the row sums
+// are accumulated with Acc<T> (exact two-float form for float), and the totals
+// are reduced in FP64 across lanes and blocks.
+template <typename T>
+struct RowAcc {
+    Acc<T> acc;
+    __device__ __forceinline__ void add_row(T s) { acc.add(s, T(1)); }
+    __device__ __forceinline__ double value() const { return acc.value(); }
+};
+
+struct Task {
+    int cond, i0, j0, jend;
+};
+
+template <int W, int TY>
+__device__ __forceinline__ Task task_of(long long t, int K, int tiles_x, int nz)
+{
+    Task r;
+    r.cond = (int)(t % K);
+    const long long sp = t / K;
+    const int ty = (int)(sp / tiles_x);
+    const int tx = (int)(sp - (long long)ty * tiles_x);
+    r.i0 = tx * W;
+    r.j0 = ty * TY;
+    r.jend = min(r.j0 + TY, nz);
+    return r;
+}
+
+__device__ __forceinline__ int wrap_col(int c, int n)
+{
+    int r = c % n;
+    return r < 0 ? r + n : r;
+}
+
+// Next task of the warp from the kernel's task counter (one atomic per task).
+__device__ __forceinline__ unsigned next_task(unsigned *ctr, int lane)
+{
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(ctr, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// Publish NV per-task sums (warp-reduced in a fixed order) at partials[t * NV + q].
+template <int NV>
+__device__ __forceinline__ void publish_task(const double (&v)[NV], double *partials, unsigned t,
+                                             int lane)
+{
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const double s = warp_sum_d(v[q]);
+        if (lane == 0) partials[(size_t)t * NV + q] = s;
+    }
+}
+
+// After every task of the launch is published: the last block (by ticket)
+// adds the per-task sums in task order, so the totals depend neither on the
+// grid nor on which warp ran which task.  Also rearms the task counter.
+template <int NV>
+__device__ __forceinline__ bool reduce_tasks(const double *partials, unsigned ntasks,
+                                             unsigned *ticket, unsigned *task_ctr,
+                                             double (&tot)[NV])
+{
+    __shared__ double red[NV][32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (unsigned t = threadIdx.x; t < ntasks; t += blockDim.x)
+            s += __ldcg(&partials[(size_t)t * NV + q]);
+        s = warp_sum_d(s);
+        if (lane == 0) red[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[q][w];
+            tot[q] = t;
+        }
+        *ticket = 0u;
+        *task_ctr = 0u;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ phase A
+//   p += alpha' u';  u = z + beta u';  v = A u;  partial u.v
+// Marching: at row jr the warp forms u(jr) and outputs v(jr - 1), which needs
+// u(jr - 2) (register), u(jr - 1) and its row neighbours (shared row) and u(jr).
+// The loads of row jr + 1 are issued before row jr is processed.
+// Shared row slot s holds column i0 - 4 + s (own columns start 16-byte aligned).
+
+template <typename T, int VEC>
+struct RowA {
+    T z[VEC], uo[VEC], D[VEC], e[VEC], n[VEC], p[VEC];
+    T hz, huo, he;
+};
+
+// One task of phase A; returns the lane's share of the task's u.v.
+template <typename T, int VEC, int TY>
+__device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, int k, bool first,
+                                             T alpha_prev, T beta, T *ub, T *ab, int lane)
+{
+    constexpr int W = 32 * VEC;
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n;
+    const T *uo_base = d.u[(k + 1) & 1];
+    T *un_base = d.u[k & 1];
+        RowAcc<T> acc;
+        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, nz);
+        const size_t off = (size_t)tk.cond * (size_t)n;
+        const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
+        const T *z = d.z + off;
+        const T *uo = uo_base + off;
+        T *un = un_base + off;
+        T *vv = d.v + off;
+        T *pp = d.p + off;
+        const T *D = d.D + coff;
+        const T *aE = d.aE + coff;
+        const T *aN = d.aN + coff;
+        const int c0 = tk.i0 + lane * VEC;
+        const bool owned = c0 < nth;
+        const int g0 = wrap_col(c0, nth);
+        const int sown = 4 + lane * VEC;
+        // halo: lane 0 -> column i0 - 1 (slot 3), lane 1 -> column i0 + W (slot W + 4)
+        const int hg = wrap_col(lane == 0 ? tk.i0 - 1 : tk.i0 + W, nth);
+        const int hslot = lane == 0 ? 3 : W + 4;
+
+        auto load_row = [&](int jr, RowA<T, VEC> &R) {
+            if (jr < 0 || jr >= nz) {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.z[q] = R.uo[q] = R.D[q] = R.e[q] = R.n[q] = R.p[q] = T(0);
+                R.hz = R.huo = R.he = T(0);
+                return;
+            }
+            const size_t q0 = (size_t)jr * nth + g0;
+            Vec<T, VEC>::ld(z + q0, R.z);
+            if (!first) {
+                Vec<T, VEC>::ld(uo + q0, R.uo);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.uo[q] = T(0);
+            }
+            Vec<T, VEC>::ld(aN + q0, R.n);
+            if (jr >= tk.j0 && jr < tk.jend) {
+                Vec<T, VEC>::ld(D + q0, R.D);
+                Vec<T, VEC>::ld(aE + q0, R.e);
+                if (!first && owned) {
+                    Vec<T, VEC>::ldrw(pp + q0, R.p);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) R.p[q] = T(0);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.D[q] = R.e[q] = R.p[q] = T(0);
+            }
+            R.hz = R.huo = R.he = T(0);
+            if (lane < 2) {
+                const size_t qh = (size_t)jr * nth + hg;
+                R.hz = __ldg(z + qh);
+                if (!first) R.huo = __ldg(uo + qh);
+                if (lane == 0) R.he = __ldg(aE + qh);
+            }
+        };
+
+        T u_m1[VEC], u_m2[VEC], uo_m1[VEC], D_m1[VEC], e_m1[VEC], n_m1[VEC], n_m2[VEC], p_m1[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q)
+            u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = T(0);
+        RowA<T, VEC> nx;
+        load_row(tk.j0 - 1, nx);
+        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+            const RowA<T, VEC> cur = nx;
+            if (jr + 1 <= tk.jend) load_row(jr + 1, nx);
+            T u[VEC];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) u[q] = first ? cur.z[q] : cur.z[q] + beta * cur.uo[q];
+            const T hu = first ? cur.hz : cur.hz + beta * cur.huo;
+            // output row jo = jr - 1: its u row and aE row are in the shared buffers
+            const int jo = jr - 1;
+            if (jo >= tk.j0 && jo < tk.jend) {
+                T vout[VEC];
+                T rowsum = T(0);
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const int s = sown + q;
+                    const T uE = (q < VEC - 1) ? u_m1[q + 1] : ub[s + 1];
+                    const T uW = (q > 0) ? u_m1[q - 1] : ub[s - 1];
+                    const T aW = (q > 0) ? e_m1[q - 1] : ab[s - 1];
+                    vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
+                              n_m2[q] * u_m2[q];
+                    rowsum += u_m1[q] * vout[q];
+                }
+                if (owned) {
+                    const size_t qo = (size_t)jo * nth + g0;
+                    Vec<T, VEC>::st(un + qo, u_m1);
+                    Vec<T, VEC>::st(vv + qo, vout);
+                    if (!first) {
+                        T pn[VEC];
+#pragma unroll
+                        for (int q = 0; q < VEC; ++q) pn[q] = p_m1[q] + alpha_prev * uo_m1[q];
+                        Vec<T, VEC>::st(pp + qo, pn);
+                    }
+                    acc.add_row(rowsum);
+                }
+            }
+            __syncwarp();
+            Vec<T, VEC>::st(ub + sown, u);
+            Vec<T, VEC>::st(ab + sown, cur.e);
+            if (lane < 2) {
+                ub[hslot] = hu;
+                if (lane == 0) ab[hslot] = cur.he;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                u_m2[q] = u_m1[q];
+                u_m1[q] = u[q];
+                uo_m1[q] = cur.uo[q];
+                n_m2[q] = n_m1[q];
+                n_m1[q] = cur.n[q];
+                D_m1[q] = cur.D[q];
+                e_m1[q] = cur.e[q];
+                p_m1[q] = cur.p[q];
+            }
+        }
+    return acc.value();
+}
+
+// Scalar update after the u.v reduction (alpha = d / u.v).
+__device__ __forceinline__ void finish_a(Scalars *sc, double uv)
+{
+    sc->pending = 0;
+    if (!finite_d(uv) || !(uv > 0.0) || !finite_d(sc->d)) {
+        sc->status = GMAF_NONFINITE;
+        sc->done = 1;
+    } else {
+        sc->alpha = sc->d / uv;
+    }
+}
+
+template <typename T, int VEC, int TY, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__restrict__ dp)
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8;
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    __shared__ __align__(16) T su[kWarps][NB];
+    __shared__ __align__(16) T sa[kWarps][NB];
+    __shared__ int s_done, s_k, s_first;
+    __shared__ double s_alpha, s_beta;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_k = sc->iter;
+        s_first = sc->first;
+        s_alpha = sc->alpha;
+        s_beta = sc->beta;
+        if (blockIdx.x == 0) {
+            // stop unless phase B's last block asks for another iteration
+            if (d.use_cond) cudaGraphSetConditional(d.cond, 0u);
+            sc->guard += 1;
+        }
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const unsigned ntasks = (unsigned)d.ntiles;
+    for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
+         t = next_task(&sc->task_ctr[0], lane)) {
+        const double val[1] = {run_task_a<T, VEC, TY>(d, t, s_k, s_first != 0, (T)s_alpha,
+                                                       (T)s_beta, su[wp], sa[wp], lane)};
+        publish_task<1>(val, d.partials, t, lane);
+    }
+    double tot[1];
+    if (reduce_tasks<1>(d.partials, ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
+        threadIdx.x == 0)
+        finish_a(sc, tot[0]);
+}
+
+// ------------------------------------------------------------------ phase B
+//   r -= alpha v;  z = M^-1 r;  partial r.z, r.r
+// Marching: at row jr the warp forms r(jr), y = D^-1 r (shared row), the first
+// ASSOR pass w(jr) (needs y(jr - 1) in registers and the row neighbours of
+// y(jr)), and the second pass z(jr - 1) (needs w(jr) in registers and the row
+// neighbours of w(jr - 1), still in the shared row).  Halo columns i0 - 2 ..
+// i0 - 1 and i0 + W .. i0 + W + 1 are formed by lanes 0..3.  The loads of row
+// jr + 1 are issued before row jr is processed.  Shared row slot s holds column
+// i0 - 4 + s.
+
+template <typename T, int VEC>
+struct RowB {
+    T r[VEC], v[VEC], dI[VEC], e[VEC], n[VEC];
+    T hr, hv, hd, he, hn;
+};
+
+// One task of phase B; writes the lane's shares of the task's r.z and r.r.
+template <typename T, int VEC, int TY, bool INIT>
+__device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int k, T alpha,
+                                           T *yb, T *wb, T *ab, int lane, double (&out)[2])
+{
+    constexpr int W = 32 * VEC;
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n;
+    const T omega = d.omega, c1 = d.c1;
+    const bool assor = (d.precond == 1);
+    const T *ro_base = d.r[k & 1];
+    T *rn_base = d.r[(k + 1) & 1];
+        RowAcc<T> arz, arr;
+        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, nz);
+        const size_t off = (size_t)tk.cond * (size_t)n;
+        const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
+        const T *ro = ro_base + off;
+        const T *vv = d.v + off;
+        T *rn = rn_base + off;
+        T *zo = d.z + off;
+        const T *invD = d.invD + coff;
+        const T *aE = d.aE + coff;
+        const T *aN = d.aN + coff;
+        const int c0 = tk.i0 + lane * VEC;
+        const bool owned = c0 < nth;
+        const int g0 = wrap_col(c0, nth);
+        const int sown = 4 + lane * VEC;
+        // halo: lanes 0..3 -> columns i0-2, i0-1 (slots 2, 3), i0+W, i0+W+1 (slots W+4, W+5)
+        const int hoff = lane < 2 ? lane - 2 : W + (lane - 2);
+        const int hg = wrap_col(tk.i0 + hoff, nth);
+        const int hslot = lane < 2 ? lane + 2 : W + 2 + lane;
+
+        auto load_row = [&](int jr, RowB<T, VEC> &R) {
+            R.hr = R.hv = R.hd = R.he = R.hn = T(0);
+            if (jr < 0 || jr >= nz) {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.r[q] = R.v[q] = R.dI[q] = R.e[q] = R.n[q] = T(0);
+                return;
+            }
+            const size_t q0 = (size_t)jr * nth + g0;
+            Vec<T, VEC>::ld(ro + q0, R.r);
+            if (!INIT) {
+                Vec<T, VEC>::ld(vv + q0, R.v);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) R.v[q] = T(0);
+            }
+            Vec<T, VEC>::ld(invD + q0, R.dI);
+            Vec<T, VEC>::ld(aE + q0, R.e);
+            Vec<T, VEC>::ld(aN + q0, R.n);
+            if (lane < 4) {
+                const size_t qh = (size_t)jr * nth + hg;
+                R.hr = __ldg(ro + qh);
+                if (!INIT) R.hv = __ldg(vv + qh);
+                R.hd = __ldg(invD + qh);
+                R.he = __ldg(aE + qh);
+                R.hn = __ldg(aN + qh);
+            }
+        };
+
+        T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
+        T hy_m1 = T(0), hn_m1 = T(0);
+        RowB<T, VEC> nx;
+        load_row(tk.j0 - 1, nx);
+        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+            const RowB<T, VEC> cur = nx;
+            if (jr + 1 <= tk.jend) load_row(jr + 1, nx);
+            const bool inrow = jr >= 0 && jr < nz;
+            T r1[VEC], y[VEC];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                r1[q] = INIT ? cur.r[q] : cur.r[q] - alpha * cur.v[q];
+                y[q] = r1[q] * cur.dI[q];
+            }
+            const T hy = (INIT ? cur.hr : cur.hr - alpha * cur.hv) * cur.hd;
+            Vec<T, VEC>::st(yb + sown, y);
+            Vec<T, VEC>::st(ab + sown, cur.e);
+            if (lane < 4) {
+                yb[hslot] = hy;
+                ab[hslot] = cur.he;
+            }
+            __syncwarp();
+            // first ASSOR pass on row jr: w = y + omega D^-1 (lower couplings) y
+            T w[VEC];
+            T hw = T(0);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) w[q] = T(0);
+            if (assor && inrow && jr >= tk.j0) {
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const int s = sown + q, gi = g0 + q;
+                    T sum = T(0);
+                    if (jr > 0) sum += n_m1[q] * y_m1[q];                            // south
+                    if (gi > 0)                                                        // west
+                        sum += ((q > 0) ? cur.e[q - 1] : ab[s - 1]) * ((q > 0) ? y[q - 1] : yb[s - 1]);
+                    if (gi == nth - 1) sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);  // east, wrapped
+                    w[q] = y[q] + omega * cur.dI[q] * sum;
+                }
+                if (lane == 1 || lane == 2) {
+                    const int s = hslot;
+                    T sum = T(0);
+                    if (jr > 0) sum += hn_m1 * hy_m1;
+                    if (hg > 0) sum += ab[s - 1] * yb[s - 1];
+                    if (hg == nth - 1) sum += cur.he * yb[s + 1];
+                    hw = hy + omega * cur.hd * sum;
+                }
+            }
+            // second pass on row jo = jr - 1: z = c1 (w + omega D^-1 (upper couplings) w)
+            const int jo = jr - 1;
+            if (jo >= tk.j0 && jo < tk.jend) {
+                T zz[VEC];
+                T rz = T(0), rr = T(0);
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    if (assor) {
+                        const int s = sown + q, gi = g0 + q;
+                        T sum = T(0);
+                        if (jo < nz - 1) sum += n_m1[q] * w[q];                                          // north
+                        if (gi < nth - 1) sum += e_m1[q] * ((q < VEC - 1) ? w_m1[q + 1] : wb[s + 1]);    // east
+                        if (gi == 0)                                                                     // west, wrapped
+                            sum += __ldg(aE + (size_t)jo * nth + nth - 1) * ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
+                        zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
+                    } else {
+                        zz[q] = y_m1[q];
+                    }
+                    rz += r_m1[q] * zz[q];
+                    rr += r_m1[q] * r_m1[q];
+                }
+                if (owned) {
+                    const size_t qo = (size_t)jo * nth + g0;
+                    Vec<T, VEC>::st(zo + qo, zz);
+                    if (!INIT) Vec<T, VEC>::st(rn + qo, r_m1);
+                    arz.add_row(rz);
+                    arr.add_row(rr);
+                }
+            }
+            __syncwarp();
+            if (assor) {
+                Vec<T, VEC>::st(wb + sown, w);
+                if (lane == 1 || lane == 2) wb[hslot] = hw;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                y_m1[q] = y[q];
+                w_m1[q] = w[q];
+                d_m1[q] = cur.dI[q];
+                n_m1[q] = cur.n[q];
+                e_m1[q] = cur.e[q];
+                r_m1[q] = r1[q];
+            }
+            hy_m1 = hy;
+            hn_m1 = cur.hn;
+        }
+    out[0] = arz.value();
+    out[1] = arr.value();
+}
+
+// Scalar update after the r.z, r.r reductions: convergence test (Eq. 3.9), beta,
+// loop guard.  Returns 1 when the run is done.
+template <bool INIT>
+__device__ __forceinline__ int finish_b(Scalars *sc, double rz, double rr, int k, double eps,
+                                        int max_iter)
+{
+    const double rel = sqrt(rr) / sc->normS;
+    sc->rel = rel;
+    int done = 0;
+    if (INIT) {
+        sc->d = rz;
+        sc->first = 1;
+        sc->pending = 0;
+        if (sc->zero_rhs) {
+            sc->converged = 1;
+            done = 1;
+        } else if (!finite_d(rz) || !finite_d(rr)) {
+            sc->status = GMAF_NONFINITE;
+            done = 1;
+        } else if (rel <= eps) {
+            sc->converged = 1;
+            done = 1;
+        } else if (sc->iter >= max_iter) {
+            done = 1;
+        }
+    } else {
+        const int it = k + 1;
+        sc->iter = it;
+        sc->first = 0;
+        sc->pending = 1;
+        if (!finite_d(rz) || !finite_d(rr)) {
+            sc->status = GMAF_NONFINITE;
+            done = 1;
+        } else if (rel <= eps) {
+            sc->converged = 1;
+            done = 1;
+        } else if (it >= max_iter) {
+            done = 1;
+        } else {
+            sc->beta = rz / sc->d;
+            sc->d = rz;
+        }
+        if (sc->guard > max_iter + 4) {   // loop guard: never more bodies than iterations
+            sc->status = GMAF_TIMEOUT;
+            done = 1;
+        }
+    }
+    sc->done = done;
+    return done;
+}
+
+template <typename T, int VEC, int TY, int MINB, bool INIT>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__restrict__ dp)
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8;
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    __shared__ __align__(16) T sy[kWarps][NB];
+    __shared__ __align__(16) T sw[kWarps][NB];
+    __shared__ __align__(16) T sa[kWarps][NB];
+    __shared__ int s_done, s_k;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_k = sc->iter;
+        s_alpha = sc->alpha;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const unsigned ntasks = (unsigned)d.ntiles;
+    for (unsigned t = next_task(&sc->task_ctr[1], lane); t < ntasks;
+         t = next_task(&sc->task_ctr[1], lane)) {
+        double val[2];
+        run_task_b<T, VEC, TY, INIT>(d, t, s_k, (T)s_alpha, sy[wp], sw[wp], sa[wp], lane, val);
+        publish_task<2>(val, d.partials, t, lane);
+    }
+    double tot[2];
+    if (reduce_tasks<2>(d.partials, ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
+        threadIdx.x == 0) {
+        const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter);
+        if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
+    }
+}
+
+// ------------------------------------------------------------------ init, finalize
+
+// r0 = b - A p0 (p0 = 0 when zero_init) into r[iter & 1]; ||b||^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_init_r(const PcgDesc<T> *__restrict__ dp)
+{
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n, N = n * d.K;
+    T *r = d.r[sc->iter & 1];
+    Acc<T> abb;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int cond = (int)(g / n);
+        const long long P = g - (long long)cond * n;
+        const T bb = d.b[g];
+        T rv = bb;
+        if (d.zero_init) {
+            d.p[g] = T(0);
+        } else {
+            const int j = (int)(P / nth), i = (int)(P - (long long)j * nth);
+            const size_t c = (size_t)d.cslot[cond] * (size_t)n + (size_t)P;
+            const size_t row = (size_t)cond * (size_t)n + (size_t)j * nth;
+            const T *p = d.p;
+            T ap = d.D[c] * p[g] - d.aE[c] * p[row + (i == nth - 1 ? 0 : i + 1)] -
+                   d.aE[c - P + (size_t)j * nth + (i == 0 ? nth - 1 : i - 1)] *
+                       p[row + (i == 0 ? nth - 1 : i - 1)];
+            if (j < nz - 1) ap -= d.aN[c] * p[g + nth];
+            if (j > 0) ap -= d.aN[c - nth] * p[g - nth];
+            rv = bb - ap;
+        }
+        r[g] = rv;
+        abb.add(bb, bb);
+    }
+    double val[1] = {abb.value()};
+    double tot[1];
+    if (reduce_last<1>(val, d.partials, &sc->ticket[kTicketInit], tot) && threadIdx.x == 0) {
+        sc->normS = sqrt(tot[0]);
+        sc->zero_rhs = (tot[0] == 0.0);
+        if (!finite_d(tot[0])) {
+            sc->status = GMAF_NONFINITE;
+            sc->done = 1;
+        }
+    }
+}
+
+// The update p += alpha u of the last iteration (deferred to phase A otherwise).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_finalize(const PcgDesc<T> *__restrict__ dp)
+{
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    if (!sc->pending) return;
+    const T alpha = (T)sc->alpha;
+    const T *u = d.u[(sc->iter + 1) & 1];
+    const long long N = d.n * d.K;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x)
+        d.p[g] += alpha * u[g];
+}
+
+static __global__ void k_reset(Scalars *sc, int keep_iter)
+{
+    if (threadIdx.x != 0) return;
+    if (!keep_iter) sc->iter = 0;
+    sc->first = 1;
+    sc->done = 0;
+    sc->converged = 0;
+    sc->status = 0;
+    sc->pending = 0;
+    sc->guard = 0;
+    sc->zero_rhs = 0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    for (int q = 0; q < 6; ++q) sc->ticket[q] = 0u;
+    sc->task_ctr[0] = 0u;
+    sc->task_ctr[1] = 0u;
+}
+
+// ------------------------------------------------------------------ FP64 residual, conversions
+
+// r = S - A p (FP64), partial ||r||^2 and ||S||^2; last block sets true_rel and rnorm.
+static __global__ void __launch_bounds__(kThreads) k_resid64(const ResidDesc *__restrict__ dp)
+{
+    const ResidDesc &d = *dp;
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n, N = n * d.K;
+    double arr = 0.0, ass = 0.0;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int cond = (int)(g / n);
+        const long long P = g - (long long)cond * n;
+        const int j = (int)(P / nth), i = (int)(P - (long long)j * nth);
+        const size_t crow = (size_t)d.cslot[cond] * (size_t)n + (size_t)j * nth;
+        const size_t row = (size_t)cond * (size_t)n + (size_t)j * nth;
+        const size_t c = crow + i;
+        const double *p = d.p;
+        const int ie = (i == nth - 1) ? 0 : i + 1, iw = (i == 0) ? nth - 1 : i - 1;
+        double ap = d.D[c] * p[g] - d.aE[c] * p[row + ie] - d.aE[crow + iw] * p[row + iw];
+        if (j < nz - 1) ap -= d.aN[c] * p[g + nth];
+        if (j > 0) ap -= d.aN[c - nth] * p[g - nth];
+        const double s = d.S[g];
+        const double rv = s - ap;
+        if (d.r) d.r[g] = rv;
+        arr = fma(rv, rv, arr);
+        ass = fma(s, s, ass);
+    }
+    double val[2] = {arr, ass};
+    double tot[2];
+    if (reduce_last<2>(val, d.partials, &d.sc->ticket[kTicketResid], tot) && threadIdx.x == 0) {
+        const double nS = sqrt(tot[1]);
+        d.sc->rnorm = sqrt(tot[0]);
+        d.sc->true_rel = (nS > 0.0) ? sqrt(tot[0]) / nS : 0.0;
+        d.sc->normS = nS;
+        if (!finite_d(tot[0]) || !finite_d(tot[1])) d.sc->status = GMAF_NONFINITE;
+    }
+}
+
+// 1/D for FP64 coefficient slots.
+static __global__ void k_invd64(const double *__restrict__ D, double *__restrict__ invD, long long m)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
+         q += (long long)gridDim.x * blockDim.x)
+        invD[q] = 1.0 / D[q];
+}
+
+// FP32 copies of the coefficient slots scaled by a power of two so that the
+// FP32 entries are of order one: A32 = scale * A.
+static __global__ void k_to_f32(const double *__restrict__ D, const double *__restrict__ aE,
+                         const double *__restrict__ aN, float *__restrict__ D32,
+                         float *__restrict__ invD32, float *__restrict__ aE32,
+                         float *__restrict__ aN32, long long m, Scalars *sc)
+{
+    const double scale = ldexp(1.0, -ilogb(D[0]));
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->scale = scale;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
+         q += (long long)gridDim.x * blockDim.x) {
+        const double dd = D[q] * scale;
+        D32[q] = (float)dd;
+        invD32[q] = (float)(1.0 / dd);
+        aE32[q] = (float)(aE[q] * scale);
+        aN32[q] = (float)(aN[q] * scale);
+    }
+}
+
+// b32 = r64 / ||r64|| (unit-norm right-hand side of the inner FP32 solve).
+static __global__ void k_make_b32(const double *__restrict__ r64, float *__restrict__ b32, long long N,
+                           const Scalars *__restrict__ outer)
+{
+    const double inv = 1.0 / outer->rnorm;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x)
+        b32[g] = (float)(r64[g] * inv);
+}
+
+// p64 += scale * ||r64|| * x32  (delta = A^-1 r64 = scale ||r64|| (scale A)^-1 (r64/||r64||)).
+static __global__ void k_update_p64(double *__restrict__ p, const float *__restrict__ x, long long N,
+                             const Scalars *__restrict__ outer)
+{
+    const double f = outer->scale * outer->rnorm;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+         g += (long long)gridDim.x * blockDim.x)
+        p[g] = fma(f, (double)x[g], p[g]);
+}
+
+
+// ------------------------------------------------------------------ batched groups
+//
+// Several joint systems ("groups": requests of uneven grids, each with its own
+// scalars, synchronized criterion and buffers) in one persistent launch per CG
+// phase.  Global task t belongs to group g with task_off[g] <= t < task_off[g+1].
+// Groups whose run is done are skipped (a device-side active mask).  Each task
+// publishes its sums at its global index and the last block reduces every
+// group over its own task range in task order, with the same order as a
+// single-group run, so a group's iterates do not depend on the other groups.
+
+constexpr int kMaxGroups = 64;
+
+template <typename T>
+struct MultiDesc {
+    int ngroups;
+    unsigned total_tasks;
+    unsigned task_off[kMaxGroups + 1];
+    const PcgDesc<T> *groups;      // device array [ngroups]
+    Scalars *msc;                  // tickets and task counters of the batched launches
+    double *partials;              // [total_tasks][2]
+};
+
+__device__ __forceinline__ int group_of(const unsigned *off, int ng, unsigned t)
+{
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block-wide sum of NV task sums over tasks [lo, hi) in task order (last block).
+template <int NV>
+__device__ __forceinline__ void reduce_range(const double *partials, unsigned lo, unsigned hi,
+                                             double (&tot)[NV])
+{
+    __shared__ double red[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (unsigned t = lo + threadIdx.x; t < hi; t += blockDim.x)
+            s += __ldcg(&partials[(size_t)t * NV + q]);
+        s = warp_sum_d(s);
+        if (lane == 0) red[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[q][w];
+            tot[q] = t;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool last_block(unsigned *ticket)
+{
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+template <typename T, int VEC, int TY, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> *__restrict__ mp)
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8;
+    const MultiDesc<T> &m = *mp;
+    __shared__ __align__(16) T su[kWarps][NB];
+    __shared__ __align__(16) T sa[kWarps][NB];
+    __shared__ int s_idle;
+    if (threadIdx.x == 0) s_idle = m.msc->done;    // every group finished earlier this round
+    __syncthreads();
+    if (s_idle) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (unsigned t = next_task(&m.msc->task_ctr[0], lane); t < m.total_tasks;
+         t = next_task(&m.msc->task_ctr[0], lane)) {
+        const int g = group_of(m.task_off, m.ngroups, t);
+        const PcgDesc<T> &d = m.groups[g];
+        int done = 0, k = 0, first = 0;
+        double alpha = 0.0, beta = 0.0;
+        if (lane == 0) {
+            done = d.sc->done;
+            k = d.sc->iter;
+            first = d.sc->first;
+            alpha = d.sc->alpha;
+            beta = d.sc->beta;
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        alpha = __shfl_sync(0xffffffffu, alpha, 0);
+        beta = __shfl_sync(0xffffffffu, beta, 0);
+        double val[1] = {0.0};
+        if (!done)
+            val[0] = run_task_a<T, VEC, TY>(d, t - m.task_off[g], k, first != 0, (T)alpha, (T)beta,
+                                            su[wp], sa[wp], lane);
+        publish_task<1>(val, m.partials, t, lane);
+    }
+    if (!last_block(&m.msc->ticket[kTicketA])) return;
+    for (int g = 0; g < m.ngroups; ++g) {
+        Scalars *sc = m.groups[g].sc;
+        const int active = !sc->done;          // unchanged since the launch began
+        double tot[1];
+        reduce_range<1>(m.partials, m.task_off[g], m.task_off[g + 1], tot);
+        if (threadIdx.x == 0 && active) {
+            sc->guard += 1;
+            finish_a(sc, tot[0]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        m.msc->ticket[kTicketA] = 0u;
+        m.msc->task_ctr[0] = 0u;
+    }
+}
+
+template <typename T, int VEC, int TY, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> *__restrict__ mp)
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8;
+    const MultiDesc<T> &m = *mp;
+    __shared__ __align__(16) T sy[kWarps][NB];
+    __shared__ __align__(16) T sw[kWarps][NB];
+    __shared__ __align__(16) T sa[kWarps][NB];
+    __shared__ int s_idle;
+    if (threadIdx.x == 0) s_idle = m.msc->done;
+    __syncthreads();
+    if (s_idle) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (unsigned t = next_task(&m.msc->task_ctr[1], lane); t < m.total_tasks;
+         t = next_task(&m.msc->task_ctr[1], lane)) {
+        const int g = group_of(m.task_off, m.ngroups, t);
+        const PcgDesc<T> &d = m.groups[g];
+        int done = 0, k = 0;
+        double alpha = 0.0;
+        if (lane == 0) {
+            done = d.sc->done;
+            k = d.sc->iter;
+            alpha = d.sc->alpha;
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        alpha = __shfl_sync(0xffffffffu, alpha, 0);
+        double val[2] = {0.0, 0.0};
+        if (!done)
+            run_task_b<T, VEC, TY, false>(d, t - m.task_off[g], k, (T)alpha, sy[wp], sw[wp], sa[wp],
+                                          lane, val);
+        publish_task<2>(val, m.partials, t, lane);
+    }
+    if (!last_block(&m.msc->ticket[kTicketB])) return;
+    int any = 0;
+    for (int g = 0; g < m.ngroups; ++g) {
+        const PcgDesc<T> &d = m.groups[g];
+        Scalars *sc = d.sc;
+        const int active = !sc->done;
+        double tot[2];
+        reduce_range<2>(m.partials, m.task_off[g], m.task_off[g + 1], tot);
+        if (threadIdx.x == 0 && active) {
+            const int done = finish_b<false>(sc, tot[0], tot[1], sc->iter, d.eps, d.max_iter);
+            any |= !done;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        m.msc->done = !any;                   // no group active any more
+        m.msc->ticket[kTicketB] = 0u;
+        m.msc->task_ctr[1] = 0u;
+    }
+}
+
+}  // namespace gmaf

@@ -31,7 +31,9 @@ GMAF_TIMEOUT = -7
 EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_bytes",
             "gmaf_last_solve_info", "gmaf_assemble", "gmaf_solve_joint", "gmaf_integrate_loads",
             "gmaf_picard_step", "gmaf_status_string", "gmaf_set_phase_timing",
-            "gmaf_phase_timing", "gmaf_solve_joint_noalloc")
+            "gmaf_phase_timing", "gmaf_solve_joint_noalloc", "gmaf_request_footprint",
+            "gmaf_server_create", "gmaf_server_destroy", "gmaf_server_submit", "gmaf_server_run",
+            "gmaf_server_poll", "gmaf_server_free_bytes")
 
 
 class gmaf_grid(ctypes.Structure):
@@ -63,6 +65,21 @@ class gmaf_solve_info(ctypes.Structure):
                 ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
                 ("kernel_variant", ctypes.c_int32), ("tasks", ctypes.c_int32)]
+
+
+class gmaf_request(ctypes.Structure):
+    _fields_ = [("grid", gmaf_grid), ("phys", gmaf_physics), ("tex", gmaf_texture),
+                ("state", gmaf_state), ("e_prev", ctypes.c_double * 4), ("dt", ctypes.c_double),
+                ("F_ext", ctypes.c_double * 4), ("d_e", ctypes.c_double),
+                ("d_edot", ctypes.c_double), ("omega", ctypes.c_double), ("eps", ctypes.c_double),
+                ("max_iter", ctypes.c_int32)]
+
+
+class gmaf_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("outer_iterations", ctypes.c_int32), ("true_rel_residual", ctypes.c_double),
+                ("state", gmaf_state), ("loads", ctypes.c_double * 12), ("J", ctypes.c_double * 48),
+                ("G", ctypes.c_double * 4)]
 
 
 class GmafError(RuntimeError):
@@ -109,6 +126,15 @@ def load(path: str = LIB_PATH):
                                            _VP, _VP, _VP, ctypes.POINTER(gmaf_solver_opts), _VP,
                                            ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_double)]
+    L.gmaf_request_footprint.argtypes = [ctypes.POINTER(gmaf_grid), ctypes.POINTER(ctypes.c_size_t)]
+    L.gmaf_server_create.argtypes = [_VP, ctypes.c_size_t, ctypes.POINTER(_VP)]
+    L.gmaf_server_destroy.argtypes = [_VP]
+    L.gmaf_server_submit.argtypes = [_VP, ctypes.POINTER(gmaf_request), ctypes.POINTER(ctypes.c_int64)]
+    L.gmaf_server_run.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32)]
+    L.gmaf_server_poll.argtypes = [_VP, ctypes.POINTER(gmaf_result), ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_int32)]
+    L.gmaf_server_free_bytes.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
     L.gmaf_status_string.argtypes = [ctypes.c_int]
     L.gmaf_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -316,6 +342,80 @@ def gmaf_solve_joint_noalloc(n_theta: int, n_z: int, n_cond: int, D, aE, aN, S, 
                                          ctypes.byref(it), ctypes.byref(rel))
     _check("gmaf_solve_joint_noalloc", st, allow)
     return st, it.value, rel.value
+
+
+def request(n_theta, n_z, phys, tex, st_vec, e_prev, dt, F_ext, d_e, d_edot, omega=1.2,
+            eps=1e-10, max_iter=100000) -> gmaf_request:
+    r = gmaf_request()
+    r.grid = grid(n_theta, n_z)
+    r.phys = physics(phys)
+    r.tex = texture(tex)
+    r.state = state(st_vec)
+    for q in range(4):
+        r.e_prev[q] = float(e_prev[q])
+        r.F_ext[q] = float(F_ext[q])
+    r.dt, r.d_e, r.d_edot = float(dt), float(d_e), float(d_edot)
+    r.omega, r.eps, r.max_iter = float(omega), float(eps), int(max_iter)
+    return r
+
+
+def gmaf_request_footprint(n_theta: int, n_z: int) -> int:
+    b = ctypes.c_size_t(0)
+    g = grid(n_theta, n_z)
+    _check("gmaf_request_footprint", load().gmaf_request_footprint(ctypes.byref(g), ctypes.byref(b)))
+    return b.value
+
+
+def result_dict(r: gmaf_result) -> dict:
+    return dict(id=r.id, status=r.status, iters=r.iterations, outer=r.outer_iterations,
+                true_rel=r.true_rel_residual, state=state_vector(r.state),
+                loads=np.array(r.loads), J=np.array(r.J).reshape(6, 8), G=np.array(r.G))
+
+
+class Server:
+    """Continuous-batching server of Picard-step requests (gmaf_server_*)."""
+
+    def __init__(self, ctx: int, hbm_budget_bytes: int):
+        h = _VP()
+        _check("gmaf_server_create", load().gmaf_server_create(_VP(ctx), int(hbm_budget_bytes),
+                                                                ctypes.byref(h)))
+        self.handle = h.value
+
+    def submit(self, req: gmaf_request) -> int:
+        i = ctypes.c_int64(0)
+        _check("gmaf_server_submit", load().gmaf_server_submit(_VP(self.handle), ctypes.byref(req),
+                                                                ctypes.byref(i)))
+        return i.value
+
+    def run(self, iterations: int):
+        a, q = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check("gmaf_server_run", load().gmaf_server_run(_VP(self.handle), int(iterations),
+                                                          ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_results: int = 64) -> list:
+        buf = (gmaf_result * max_results)()
+        n = ctypes.c_int32(0)
+        _check("gmaf_server_poll", load().gmaf_server_poll(_VP(self.handle), buf, max_results,
+                                                            ctypes.byref(n)))
+        return [result_dict(buf[i]) for i in range(n.value)]
+
+    def free_bytes(self) -> int:
+        b = ctypes.c_size_t(0)
+        _check("gmaf_server_free_bytes", load().gmaf_server_free_bytes(_VP(self.handle),
+                                                                        ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if self.handle:
+            _check("gmaf_server_destroy", load().gmaf_server_destroy(_VP(self.handle)))
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Context:

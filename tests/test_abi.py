@@ -63,6 +63,10 @@ int main(void) {
   printf("gmaf_state %zu\n", sizeof(gmaf_state));
   printf("gmaf_solver_opts %zu\n", sizeof(gmaf_solver_opts));
   printf("gmaf_solve_info %zu\n", sizeof(gmaf_solve_info));
+  printf("gmaf_request %zu\n", sizeof(gmaf_request));
+  printf("gmaf_result %zu\n", sizeof(gmaf_result));
+  P(gmaf_request, state) P(gmaf_request, dt) P(gmaf_request, max_iter)
+  P(gmaf_result, state) P(gmaf_result, J) P(gmaf_result, G)
   P(gmaf_texture, radius) P(gmaf_texture, offset_z) P(gmaf_state, edot)
   P(gmaf_solver_opts, omega) P(gmaf_solver_opts, eps) P(gmaf_solver_opts, max_iter)
   P(gmaf_solver_opts, precision) P(gmaf_solver_opts, zero_init)
@@ -83,7 +87,7 @@ def test_ctypes_structs_match_header(tmp_path):
     got = dict(line.rsplit(" ", 1) for line in subprocess.run(
         [str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
     for name in ("gmaf_grid", "gmaf_physics", "gmaf_texture", "gmaf_state", "gmaf_solver_opts",
-                 "gmaf_solve_info"):
+                 "gmaf_solve_info", "gmaf_request", "gmaf_result"):
         assert int(got[name]) == ctypes.sizeof(getattr(gmaf, name)), name
     for key, v in got.items():
         if "." in key:
