@@ -274,6 +274,12 @@ int gmaf_server_poll(gmaf_server *server, gmaf_result *out, int32_t max_results,
 /* Free bytes left in the server's arena. */
 int gmaf_server_free_bytes(const gmaf_server *server, size_t *bytes_out);
 
+/* Copy the 9 pressure fields of the last gmaf_picard_step on this context
+ * (condition-major, 9 * n_z * n_theta doubles, device memory p_out) for a
+ * step of the given grid; GMAF_INVALID_ARG if the last step had another grid.
+ * Asynchronous. */
+int gmaf_last_fields(gmaf_ctx *ctx, const gmaf_grid *grid, double *p_out);
+
 /* Static description of a status code. */
 const char *gmaf_status_string(int status);
 

@@ -135,6 +135,9 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     c->no_tune = (nt && nt[0] == '1') ? 1 : 0;
     const char *fv = std::getenv("GMAF_VARIANT");
     c->force_variant = fv ? std::atoi(fv) : -1;
+    const char *ie = std::getenv("GMAF_INNER_EPS");
+    c->inner_floor = ie ? std::atof(ie) : 1e-6;
+    if (!(c->inner_floor > 0.0 && c->inner_floor < 0.5)) c->inner_floor = 1e-6;
     *out = c;
     return GMAF_OK;
 }
@@ -188,6 +191,14 @@ int gmaf_phase_timing(const gmaf_ctx *c, double ms_out[4], int64_t launches_out[
         launches_out[q] = c->phase_count[q];
     }
     return GMAF_OK;
+}
+
+int gmaf_last_fields(gmaf_ctx *c, const gmaf_grid *grid, double *p_out)
+{
+    if (!c || !grid || !p_out || !c->buf[B_PP]) return GMAF_INVALID_ARG;
+    if (grid->n_theta != c->pp_nth || grid->n_z != c->pp_nz) return GMAF_INVALID_ARG;
+    const size_t bytes = (size_t)9 * grid->n_theta * grid->n_z * sizeof(double);
+    return cuda_status(cudaMemcpyAsync(p_out, c->buf[B_PP], bytes, cudaMemcpyDeviceToDevice, c->stream));
 }
 
 int gmaf_workspace_bytes(const gmaf_ctx *c, size_t *bytes_out)

@@ -131,6 +131,7 @@ struct gmaf_ctx {
     gmaf::TuneEntry tune[gmaf::kTuneEntries];
     int ntune, tune_next;
     int pp_nth, pp_nz;             // shape of the Picard-step fields held in B_PP
+    double inner_floor;            // smallest relative residual asked of an inner FP32 solve
 };
 
 namespace gmaf {

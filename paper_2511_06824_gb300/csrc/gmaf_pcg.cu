@@ -34,10 +34,10 @@ namespace gmaf {
 
 // ------------------------------------------------------------------ host driver
 
-static int grid_for(const void *kernel, long long work_items, int num_sms)
+static int grid_for(const void *kernel, long long work_items, int num_sms, size_t smem = 0)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     long long g = (long long)per_sm * num_sms;
@@ -69,6 +69,7 @@ template <typename T>
 struct KernelSet {
     const void *a, *b, *b_init;
     int W, TY, id;
+    size_t smem_b;             // dynamic shared memory of the phase-B kernels
 };
 
 template <typename T, int VEC, int TY, int MINB>
@@ -77,34 +78,54 @@ static KernelSet<T> ks_of(int)
     return {(const void *)k_phase_a<T, VEC, TY, MINB>,
             (const void *)k_phase_b<T, VEC, TY, MINB, false>,
             (const void *)k_phase_b<T, VEC, TY, MINB, true>, 32 * VEC, TY,
-            1000 * VEC + 10 * TY + MINB};
+            1000 * VEC + 10 * TY + MINB, 0};
 }
 
-constexpr int kMaxVariants = 8;
+// Phase B staged through shared memory D rows ahead (cp.async); id + 100000 D.
+template <typename T, int VEC, int TY, int MINB, int D>
+static KernelSet<T> ks_staged()
+{
+    const size_t smem = (size_t)kWarps * RingB<T, VEC>::per_warp(D) * sizeof(T);
+    const void *b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, D>;
+    const void *bi = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, D>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(bi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaGetLastError();
+        attr = true;
+    }
+    return {(const void *)k_phase_a<T, VEC, TY, MINB>, b, bi, 32 * VEC, TY,
+            100000 * D + 1000 * VEC + 10 * TY + MINB, smem};
+}
+
+constexpr int kMaxVariants = 10;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
-static int variants(KernelSet<float> *out, bool vec_ok)
+static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
 {
     int n = 0;
     if (vec_ok) {
         out[n++] = ks_of<float, 4, 32, 2>(0);
+        out[n++] = ks_staged<float, 4, 32, 2, 2>();
+        out[n++] = ks_staged<float, 4, 32, 3, 2>();
+        out[n++] = ks_staged<float, 4, 16, 3, 2>();
         out[n++] = ks_of<float, 4, 16, 2>(0);
-        out[n++] = ks_of<float, 4, 16, 3>(1);
         out[n++] = ks_of<float, 2, 32, 4>(2);
-        out[n++] = ks_of<float, 2, 16, 4>(3);
     }
+    if (vec8_ok) out[n++] = ks_staged<float, 8, 32, 2, 1>();
     out[n++] = ks_of<float, 1, 32, 4>(4);
     out[n++] = ks_of<float, 1, 16, 4>(5);
     return n;
 }
 
-static int variants(KernelSet<double> *out, bool vec_ok)
+static int variants(KernelSet<double> *out, bool vec_ok, bool = false)
 {
     int n = 0;
     if (vec_ok) {
         out[n++] = ks_of<double, 2, 32, 2>(0);
+        out[n++] = ks_staged<double, 2, 32, 2, 2>();
         out[n++] = ks_of<double, 2, 16, 2>(0);
-        out[n++] = ks_of<double, 2, 16, 3>(1);
     }
     out[n++] = ks_of<double, 1, 32, 3>(4);
     out[n++] = ks_of<double, 1, 16, 3>(5);
@@ -123,12 +144,19 @@ static bool vec_ok(const PcgDesc<T> &h)
     return ok;
 }
 
+// VEC = 8 float kernels: two 16-byte chunks per lane, n_theta % 8 == 0.
+template <typename T>
+static bool vec8_ok(const PcgDesc<T> &h)
+{
+    return sizeof(T) == 4 && vec_ok(h) && (h.nth % 8) == 0;
+}
+
 // Default choice without tuning: the first candidate.
 template <typename T>
 static KernelSet<T> choose_kernels(const PcgDesc<T> &h)
 {
     KernelSet<T> c[kMaxVariants];
-    variants(c, vec_ok(h));
+    variants(c, vec_ok(h), vec8_ok(h));
     return c[0];
 }
 
@@ -141,10 +169,11 @@ struct PcgRun {
 };
 
 template <typename T>
-static cudaError_t launch(const void *fn, int grid, const PcgDesc<T> *dd, cudaStream_t s)
+static cudaError_t launch(const void *fn, int grid, const PcgDesc<T> *dd, cudaStream_t s,
+                         size_t smem = 0)
 {
     void *args[] = {(void *)&dd};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, s);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 static bool graph_matches(const GraphCache &gc, int ga, int gb, int gs, const void *desc,
@@ -177,6 +206,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     if (e == cudaSuccess) {
         kp.func = (void *)run.ks.b_init;
         kp.gridDim = dim3(run.grid_b);
+        kp.sharedMemBytes = (unsigned)run.ks.smem_b;
         e = cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp);
     }
     cudaGraphNodeParams cp{};
@@ -189,16 +219,19 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         kp.func = (void *)run.ks.a;
         kp.gridDim = dim3(run.grid_a);
+        kp.sharedMemBytes = 0;
         e = cudaGraphAddKernelNode(&n_a, body, nullptr, 0, &kp);
         if (e == cudaSuccess) {
             kp.func = (void *)run.ks.b;
             kp.gridDim = dim3(run.grid_b);
+            kp.sharedMemBytes = (unsigned)run.ks.smem_b;
             e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
         }
     }
     if (e == cudaSuccess) {
         kp.func = (void *)k_finalize<T>;
         kp.gridDim = dim3(run.grid_s);
+        kp.sharedMemBytes = 0;
         e = cudaGraphAddKernelNode(&n_fin, g, &n_while, 1, &kp);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec, g, 0);
@@ -219,9 +252,9 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
 
 // Blocks for a persistent phase kernel: enough to hold every task's warp, at
 // most what stays resident.
-static int phase_grid(const void *kernel, long long ntasks, int num_sms)
+static int phase_grid(const void *kernel, long long ntasks, int num_sms, size_t smem = 0)
 {
-    return grid_for(kernel, (ntasks + kWarps - 1) / kWarps, num_sms);
+    return grid_for(kernel, (ntasks + kWarps - 1) / kWarps, num_sms, smem);
 }
 
 template <typename T>
@@ -233,7 +266,7 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
     h.tiles_y = (h.nz + ks.TY - 1) / ks.TY;
     h.ntiles = (long long)h.tiles_x * h.tiles_y * h.K;
     run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms);
-    run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms);
+    run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b);
     run.grid_s = stream_grid(h.n * h.K, ctx->num_sms);
 }
 
@@ -273,12 +306,12 @@ static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand
             GMAF_CUDA(cudaMemcpyAsync(tr.d_desc, &tr.h, sizeof(PcgDesc<T>), cudaMemcpyHostToDevice, s));
             k_reset<<<1, 32, 0, s>>>(tr.h.sc, 0);
             k_init_r<T><<<tr.grid_s, kThreads, 0, s>>>(tr.d_desc);
-            GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s));
+            GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s, tr.ks.smem_b));
             const int warm = 3, reps = 10;
             for (int q = 0; q < warm + reps; ++q) {
                 if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
                 GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s));
-                GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s));
+                GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s, tr.ks.smem_b));
             }
             GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
             GMAF_CUDA(cudaEventSynchronize(ctx->ev[1]));
@@ -303,7 +336,7 @@ static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
     run.d_desc = desc_slot;
     KernelSet<T> cand[kMaxVariants];
     const bool vo = vec_ok(h);
-    const int ncand = variants(cand, vo);
+    const int ncand = variants(cand, vo, vec8_ok(h));
     int pick = 0;
     TuneEntry key{};
     key.tsize = (int)sizeof(T);
@@ -412,7 +445,7 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
     int *done_h = (int *)ctx->pinned;
     PhaseClock clk{ctx};
     clk.begin(s);
-    GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s));
+    GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s, run.ks.smem_b));
     clk.end(s, 2);
     const int chunk = 16;
     for (int it = 0; it <= run.h.max_iter + chunk; it += chunk) {
@@ -425,7 +458,7 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
             GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s));
             clk.end(s, 0);
             clk.begin(s);
-            GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s));
+            GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s, run.ks.smem_b));
             clk.end(s, 1);
         }
     }
@@ -612,7 +645,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     rd.r = (double *)ctx->buf[B_R64];
     GMAF_CUDA(cudaMemcpyAsync(d_rdesc, &rd, sizeof(ResidDesc), cudaMemcpyHostToDevice, s));
 
-    const double inner_floor = 1e-5;
+    const double inner_floor = ctx->inner_floor;
     const int max_outer = 12;
     int total_inner = 0, outer = 0;
     bool tuned = false;
@@ -795,7 +828,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     h.tiles_y = (nz + ks.TY - 1) / ks.TY;
     h.ntiles = (long long)h.tiles_x * h.tiles_y * K;
     const int grid_a = phase_grid(ks.a, h.ntiles, num_sms);
-    const int grid_b = phase_grid(ks.b, h.ntiles, num_sms);
+    const int grid_b = phase_grid(ks.b, h.ntiles, num_sms, ks.smem_b);
     const int grid_s = stream_grid(N, num_sms);
     long long np = 2 * h.ntiles;
     if (2LL * grid_s > np) np = 2LL * grid_s;
@@ -837,7 +870,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     for (;;) {
         k_reset<<<1, 32, 0, s>>>(dsc, keep ? 1 : 0);
         if (init_r) k_init_r<double><<<grid_s, kThreads, 0, s>>>(d_desc);
-        e = launch<double>(ks.b_init, grid_b, d_desc, s);
+        e = launch<double>(ks.b_init, grid_b, d_desc, s, ks.smem_b);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
         const int chunk = 16;
@@ -849,7 +882,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
             if (done) break;
             for (int q = 0; q < chunk && e == cudaSuccess; ++q) {
                 e = launch<double>(ks.a, grid_a, d_desc, s);
-                if (e == cudaSuccess) e = launch<double>(ks.b, grid_b, d_desc, s);
+                if (e == cudaSuccess) e = launch<double>(ks.b, grid_b, d_desc, s, ks.smem_b);
             }
             if (e != cudaSuccess) return cuda_status(e);
         }

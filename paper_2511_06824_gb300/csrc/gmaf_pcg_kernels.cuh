@@ -154,6 +154,26 @@ struct Vec<float, 4> {
     }
 };
 template <>
+struct Vec<float, 8> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[8])
+    {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    }
+    static __device__ __forceinline__ void ldrw(const float *p, float (&x)[8])
+    {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        const float4 b = *(reinterpret_cast<const float4 *>(p) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[8])
+    {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(x[4], x[5], x[6], x[7]);
+    }
+};
+template <>
 struct Vec<float, 2> {
     static __device__ __forceinline__ void ld(const float *p, float (&x)[2])
     {
@@ -908,6 +928,271 @@ static __global__ void k_update_p64(double *__restrict__ p, const float *__restr
         p[g] = fma(f, (double)x[g], p[g]);
 }
 
+
+// ------------------------------------------------------------------ phase B, staged rows
+//
+// Same arithmetic and order as run_task_b, but the five input rows (r, v, 1/D,
+// aE, aN with their halo columns) are staged by cp.async into a per-warp ring of
+// D + 1 rows in shared memory, D rows ahead of the row being processed, so the
+// loads in flight do not occupy registers.  One commit group per row (empty
+// groups keep the count uniform); row jr is consumed after wait_group(D).
+// 16-byte copies need VEC * sizeof(T) == 16 and aligned rows.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *s, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *s, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(s)), "l"(g), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T, int VEC>
+struct RingB {
+    static constexpr int W = 32 * VEC, NB = W + 8, NF = 5;
+    // elements per warp: (D+1) staged rows of NF fields, plus the y and w rows
+    __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
+};
+
+// EDGE = false: the strip and its halo touch neither theta edge (2 <= i0 and
+// i0 + W + 2 <= n_theta), so no periodic-wrap rule can apply and the tests are
+// compiled out.
+template <typename T, int VEC, int TY, bool INIT, int D, bool EDGE>
+__device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Task &tk, int k,
+                                                  T alpha, T *ring, T *yb, T *wb, int lane,
+                                                  double (&out)[2])
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8, NF = 5, SLOT = NF * NB;
+    constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
+    static_assert(VEC % CH == 0, "whole 16-byte chunks per lane");
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n;
+    const T omega = d.omega, c1 = d.c1;
+    const bool assor = (d.precond == 1);
+    RowAcc<T> arz, arr;
+    const size_t off = (size_t)tk.cond * (size_t)n;
+    const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
+    const int c0 = tk.i0 + lane * VEC;
+    const bool owned = c0 < nth;
+    const int g0 = EDGE ? wrap_col(c0, nth) : c0;
+    const int sown = 4 + lane * VEC;
+    const int hoff = lane < 2 ? lane - 2 : W + (lane - 2);
+    const int hg = EDGE ? wrap_col(tk.i0 + hoff, nth) : tk.i0 + hoff;
+    const int hslot = lane < 2 ? lane + 2 : W + 2 + lane;
+    // row pointers at row j0 - 1 (own columns / halo column); advanced by n_theta per row
+    const long long row0 = (long long)(tk.j0 - 1) * nth;
+    const T *src[NF] = {d.r[k & 1] + off, d.v + off, d.invD + coff, d.aE + coff, d.aN + coff};
+    T *rn = d.r[(k + 1) & 1] + off + (long long)tk.j0 * nth + g0;
+    T *zo = d.z + off + (long long)tk.j0 * nth + g0;
+    const T *aE = d.aE + coff;
+
+    auto issue = [&](int jr) {
+        if (jr >= 0 && jr < nz && jr <= tk.jend) {
+            T *slot = ring + ((jr + 1) % (D + 1)) * SLOT;
+            const long long rq = row0 + (long long)(jr - tk.j0 + 1) * nth;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (INIT && f == 1) continue;
+#pragma unroll
+                for (int c = 0; c < VEC; c += CH) cp_async16(slot + f * NB + sown + c, src[f] + rq + g0 + c);
+            }
+            if (lane < 4) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (INIT && f == 1) continue;
+                    cp_async_small<sizeof(T)>(slot + f * NB + hslot, src[f] + rq + hg);
+                }
+            }
+        }
+        cp_commit();
+    };
+
+    T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
+    T hy_m1 = T(0), hn_m1 = T(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
+    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+        issue(jr + D);
+        cp_wait<D>();
+        __syncwarp();
+        const T *cur = ring + ((jr + 1) % (D + 1)) * SLOT;
+        const bool inrow = jr >= 0 && jr < nz;
+        T r1[VEC], y[VEC], dI[VEC], ev[VEC], nv[VEC];
+        T hy = T(0), hd = T(0), he = T(0), hn = T(0);
+        if (inrow) {
+            T rv[VEC], vx[VEC];
+            Vec<T, VEC>::ldrw(cur + 0 * NB + sown, rv);
+            if (!INIT) Vec<T, VEC>::ldrw(cur + 1 * NB + sown, vx);
+            Vec<T, VEC>::ldrw(cur + 2 * NB + sown, dI);
+            Vec<T, VEC>::ldrw(cur + 3 * NB + sown, ev);
+            Vec<T, VEC>::ldrw(cur + 4 * NB + sown, nv);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                r1[q] = INIT ? rv[q] : rv[q] - alpha * vx[q];
+                y[q] = r1[q] * dI[q];
+            }
+            if (lane < 4) {
+                const T hr = INIT ? cur[hslot] : cur[hslot] - alpha * cur[NB + hslot];
+                hd = cur[2 * NB + hslot];
+                he = cur[3 * NB + hslot];
+                hn = cur[4 * NB + hslot];
+                hy = hr * hd;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) r1[q] = y[q] = dI[q] = ev[q] = nv[q] = T(0);
+        }
+        Vec<T, VEC>::st(yb + sown, y);
+        if (lane < 4) yb[hslot] = hy;
+        __syncwarp();
+        T w[VEC];
+        T hw = T(0);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) w[q] = T(0);
+        if (assor && inrow && jr >= tk.j0) {
+            const T *ab = cur + 3 * NB;          // aE of row jr with its halo
+            const bool south = jr > 0;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const int s = sown + q;
+                T sum = south ? n_m1[q] * y_m1[q] : T(0);
+                const T aW = (q > 0) ? ev[q - 1] : ab[s - 1];
+                const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
+                if (!EDGE) {
+                    sum += aW * yW;
+                } else {
+                    const int gi = g0 + q;
+                    if (gi > 0) sum += aW * yW;
+                    if (gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
+                }
+                w[q] = y[q] + omega * dI[q] * sum;
+            }
+            if (lane == 1 || lane == 2) {
+                const int s = hslot;
+                T sum = south ? hn_m1 * hy_m1 : T(0);
+                if (!EDGE) {
+                    sum += ab[s - 1] * yb[s - 1];
+                } else {
+                    if (hg > 0) sum += ab[s - 1] * yb[s - 1];
+                    if (hg == nth - 1) sum += he * yb[s + 1];
+                }
+                hw = hy + omega * hd * sum;
+            }
+        }
+        const int jo = jr - 1;
+        if (jo >= tk.j0 && jo < tk.jend) {
+            T zz[VEC];
+            T rz = T(0), rr = T(0);
+            const bool north = jo < nz - 1;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                if (assor) {
+                    const int s = sown + q;
+                    T sum = north ? n_m1[q] * w[q] : T(0);
+                    const T wE = (q < VEC - 1) ? w_m1[q + 1] : wb[s + 1];
+                    if (!EDGE) {
+                        sum += e_m1[q] * wE;
+                    } else {
+                        const int gi = g0 + q;
+                        if (gi < nth - 1) sum += e_m1[q] * wE;
+                        if (gi == 0)
+                            sum += __ldg(aE + (size_t)jo * nth + nth - 1) * ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
+                    }
+                    zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
+                } else {
+                    zz[q] = y_m1[q];
+                }
+                rz += r_m1[q] * zz[q];
+                rr += r_m1[q] * r_m1[q];
+            }
+            if (owned) {
+                Vec<T, VEC>::st(zo, zz);
+                if (!INIT) Vec<T, VEC>::st(rn, r_m1);
+                arz.add_row(rz);
+                arr.add_row(rr);
+            }
+            zo += nth;
+            rn += nth;
+        }
+        __syncwarp();
+        if (assor) {
+            Vec<T, VEC>::st(wb + sown, w);
+            if (lane == 1 || lane == 2) wb[hslot] = hw;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            y_m1[q] = y[q];
+            w_m1[q] = w[q];
+            d_m1[q] = dI[q];
+            n_m1[q] = nv[q];
+            e_m1[q] = ev[q];
+            r_m1[q] = r1[q];
+        }
+        hy_m1 = hy;
+        hn_m1 = hn;
+    }
+    cp_wait<0>();
+    __syncwarp();
+    out[0] = arz.value();
+    out[1] = arr.value();
+}
+
+template <typename T, int VEC, int TY, int MINB, bool INIT, int D>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc<T> *__restrict__ dp)
+{
+    using R = RingB<T, VEC>;
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    extern __shared__ __align__(16) unsigned char g_dyn_smem[];
+    __shared__ int s_done, s_k;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_k = sc->iter;
+        s_alpha = sc->alpha;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *mine = reinterpret_cast<T *>(g_dyn_smem) + (size_t)wp * R::per_warp(D);
+    T *ring = mine;
+    T *yb = mine + (D + 1) * R::NF * R::NB;
+    T *wb = yb + R::NB;
+    const unsigned ntasks = (unsigned)d.ntiles;
+    constexpr int W = 32 * VEC;
+    for (unsigned t = next_task(&sc->task_ctr[1], lane); t < ntasks;
+         t = next_task(&sc->task_ctr[1], lane)) {
+        double val[2];
+        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+        if (tk.i0 >= 2 && tk.i0 + W + 2 <= d.nth)
+            run_task_b_staged<T, VEC, TY, INIT, D, false>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
+        else
+            run_task_b_staged<T, VEC, TY, INIT, D, true>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
+        publish_task<2>(val, d.partials, t, lane);
+    }
+    double tot[2];
+    if (reduce_tasks<2>(d.partials, ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
+        threadIdx.x == 0) {
+        const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter);
+        if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
+    }
+}
 
 // ------------------------------------------------------------------ batched groups
 //

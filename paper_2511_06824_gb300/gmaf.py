@@ -33,7 +33,7 @@ EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_by
             "gmaf_picard_step", "gmaf_status_string", "gmaf_set_phase_timing",
             "gmaf_phase_timing", "gmaf_solve_joint_noalloc", "gmaf_request_footprint",
             "gmaf_server_create", "gmaf_server_destroy", "gmaf_server_submit", "gmaf_server_run",
-            "gmaf_server_poll", "gmaf_server_free_bytes")
+            "gmaf_server_poll", "gmaf_server_free_bytes", "gmaf_last_fields")
 
 
 class gmaf_grid(ctypes.Structure):
@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH):
     L.gmaf_server_poll.argtypes = [_VP, ctypes.POINTER(gmaf_result), ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_int32)]
     L.gmaf_server_free_bytes.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
+    L.gmaf_last_fields.argtypes = [_VP, ctypes.POINTER(gmaf_grid), _VP]
     L.gmaf_status_string.argtypes = [ctypes.c_int]
     L.gmaf_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -306,6 +307,13 @@ def gmaf_picard_step(ctx: int, n_theta: int, n_z: int, phys, tex, st_vec, e_prev
     _check("gmaf_picard_step", rc, allow)
     return dict(status=rc, state=state_vector(s), loads=loads, J=J.reshape(6, 8), G=G,
                 iters=it.value)
+
+
+def gmaf_last_fields(ctx: int, n_theta: int, n_z: int, p_out) -> None:
+    """Copy the 9 pressure fields of the last Picard step into a float64 CUDA tensor."""
+    g = grid(n_theta, n_z)
+    _check("gmaf_last_fields", load().gmaf_last_fields(_VP(ctx), ctypes.byref(g),
+                                                        _dev(p_out, 9 * n_theta * n_z, "p_out")))
 
 
 def gmaf_set_phase_timing(ctx: int, on: bool) -> None:

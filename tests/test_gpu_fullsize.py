@@ -1,0 +1,115 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (gmaf_picard_step, ASSOR-II, autotuned kernels, graph loop).
+
+512 x 256 x 9 smooth, FP64: the whole Picard step against the oracle's.
+2048 x 1024 x 9 textured, mixed precision (the benchmark workload): the oracle
+cannot solve it in test time, so the step is checked through properties the
+oracle computes from the GPU's own pressure fields -- the true residual with the
+oracle's matrix, the loads and the 6 x 8 Jacobian from the oracle's integration,
+the generalized force and the state update from numpy's 4 x 4 solve -- and the
+assembly against the oracle's entry by entry.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_06824_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = (60.0 / 600.0) / 360.0
+F_EXT = np.array([40.0, -20.0, 8.0, -4.0])
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_06824_gb300 import build, gmaf
+    build.build()
+    gmaf.load()
+    return gmaf
+
+
+def load_err(a, b):
+    out = 0.0
+    for part in (slice(0, 6), slice(6, 12)):
+        x, y = np.asarray(a)[..., part], np.asarray(b)[..., part]
+        nrm = np.linalg.norm(y, axis=-1, keepdims=True)
+        out = max(out, float(np.max(np.abs(x - y) / np.maximum(np.abs(y), 1e-3 * nrm))))
+    return out
+
+
+def conditions(w):
+    conds = [w.state.copy() for _ in range(9)]
+    for j in range(4):
+        conds[1 + j][j] += w.d_e
+        conds[5 + j][4 + j] += w.d_edot
+    return conds
+
+
+def test_picard_step_512x256x9_fp64_matches_oracle(g):
+    w = inputs.make("smooth-512x256-k9", 0)
+    e_prev = w.state[:4].copy()
+    with g.Context() as c:
+        r = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state, e_prev, DT,
+                               F_EXT, w.d_e, w.d_edot, g.solver_opts(eps=w.eps, precision=0))
+    o = oracle.picard_step(w.n_theta, w.n_z, w.phys, w.tex, w.state, e_prev, DT, F_EXT, w.d_e,
+                           w.d_edot, eps=w.eps)
+    assert r["status"] == 0 and o["status"] == 0
+    assert load_err(r["loads"], o["loads"]) <= 1e-7
+    colscale = np.abs(o["J"]).max(axis=0, keepdims=True)
+    assert np.max(np.abs(r["J"] - o["J"]) / colscale) <= 1e-4
+    np.testing.assert_allclose(r["G"], o["G"], rtol=1e-6, atol=1e-6 * np.abs(o["G"]).max())
+    ds_g, ds_o = r["state"] - w.state, o["state"] - w.state
+    assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o)
+
+
+def test_benchmark_workload_step_properties(g):
+    w = inputs.make("textured-2048x1024-k9", 0)
+    nth, nz, n = w.n_theta, w.n_z, w.n
+    e_prev = w.state[:4].copy()
+    conds = conditions(w)
+    with g.Context() as c:
+        r = g.gmaf_picard_step(c.handle, nth, nz, w.phys, w.tex, w.state, e_prev, DT, F_EXT,
+                               w.d_e, w.d_edot, g.solver_opts(eps=w.eps, precision=1))
+        p = torch.zeros(9 * n, dtype=torch.float64, device="cuda")
+        g.gmaf_last_fields(c.handle, nth, nz, p)
+        # assembly of the same 9 conditions through the ABI
+        D, aE, aN, S = (torch.zeros(9 * n, dtype=torch.float64, device="cuda") for _ in range(4))
+        g.gmaf_assemble(c.handle, nth, nz, w.phys, w.tex, conds, D, aE, aN, S)
+        torch.cuda.synchronize()
+        info = g.gmaf_last_solve_info(c.handle)
+    assert r["status"] == 0
+    pg = p.cpu().numpy().reshape(9, nz, nth)
+    so, Do, aEo, aNo, So = oracle.assemble_joint(nth, nz, w.phys, w.tex, conds)
+    assert so == 0
+    # assembly, entry by entry
+    np.testing.assert_allclose(aE.cpu().numpy().reshape(9, nz, nth), aEo, rtol=1e-11)
+    np.testing.assert_allclose(aN.cpu().numpy().reshape(9, nz, nth), aNo, rtol=1e-11)
+    np.testing.assert_allclose(D.cpu().numpy().reshape(9, nz, nth), Do, rtol=1e-11)
+    Sg = S.cpu().numpy().reshape(9, nz, nth)
+    np.testing.assert_allclose(Sg, So, rtol=1e-9, atol=1e-9 * np.abs(So[:, 1:-1]).max())
+    # Eq. 3.9 with the oracle's matrix on the GPU's fields
+    Ap = oracle.apply_matrix(nth, nz, Do, aEo, aNo, pg)
+    rel = np.linalg.norm(So.ravel() - Ap) / np.linalg.norm(So.ravel())
+    assert rel <= 10 * w.eps, rel
+    assert abs(info["true_rel_residual"] - rel) <= 1e-3 * rel + 1e-13
+    # loads and Jacobian from the oracle's integration of the same fields
+    L = np.stack([oracle.loads(nth, nz, w.phys, w.tex, conds[k], pg[k])[1] for k in range(9)])
+    assert load_err(r["loads"], L[0]) <= 1e-9
+    F = L[:, :6] + L[:, 6:]
+    J = np.stack([(F[1 + c] - F[0]) / (w.d_e if c < 4 else w.d_edot) for c in range(8)], axis=1)
+    colscale = np.abs(J).max(axis=0, keepdims=True)
+    assert np.max(np.abs(r["J"] - J) / colscale) <= 1e-6
+    # generalized force and update (Eq. 2.12 with the backward-difference closure)
+    Lg = w.phys[1]
+    T = np.array([[1, 0, 0, 0, -1 / Lg, 0], [0, 1, 0, 1 / Lg, 0, 0], [0, 0, 0, 0, 1 / Lg, 0],
+                  [0, 0, 0, -1 / Lg, 0, 0]])
+    G = T @ F[0] + F_EXT
+    np.testing.assert_allclose(r["G"], G, rtol=1e-8, atol=1e-8 * np.abs(G).max())
+    Je, Jd = T @ r["J"][:, :4], T @ r["J"][:, 4:]
+    delta = np.linalg.solve(Jd + DT * Je, -r["G"] - Je @ (e_prev + DT * w.state[4:] - w.state[:4]))
+    np.testing.assert_allclose(r["state"][4:], w.state[4:] + delta, rtol=1e-9, atol=1e-18)
+    np.testing.assert_allclose(r["state"][:4], e_prev + DT * r["state"][4:], rtol=1e-12)
