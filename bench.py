@@ -149,7 +149,7 @@ class ClockSampler:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("gmaf_pcg.cu", "gmaf_internal.cuh"):
+    for f in ("gmaf_pcg.cu", "gmaf_pcg_kernels.cuh", "gmaf_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2511_06824_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

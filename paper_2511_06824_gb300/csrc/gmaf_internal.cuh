@@ -53,6 +53,7 @@ template <typename T>
 struct PcgDesc {
     int nth, nz, K, tiles_x, tiles_y, precond, zero_init, use_cond;
     long long n, ntiles;
+    long long sgroups;             // row groups of the static schedule
     const T *D, *invD, *aE, *aN;   // coefficient slots, [slot][n]
     const int *cslot;              // coefficient slot of each condition, [K]
     const T *b;                    // right-hand side, [K][n]
@@ -63,7 +64,7 @@ struct PcgDesc {
     int max_iter;
     cudaGraphConditionalHandle cond;
     Scalars *sc;
-    double *partials;              // per-task sums [ntiles][2], or per-block [2][grid]
+    double *partials;              // per-task (or per-warp) sums [ntiles][2], or per-block [2][grid]
 };
 
 // FP64 residual r = S - A p over all conditions, with ||r||^2 and ||S||^2.

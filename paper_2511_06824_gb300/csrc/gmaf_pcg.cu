@@ -23,6 +23,7 @@
 // T = double (FP64 mode) or float (inner solve of the mixed-precision mode, whose
 // dot products are accumulated exactly per thread in two-float form and reduced in
 // FP64).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -64,21 +65,24 @@ static int stream_grid(long long N, int num_sms)
 #define GMAF_CUDA(x) GMAF_TRY(cuda_status(x))
 
 // The phase kernels of one run: strip width W = 32 * VEC, TY rows per task,
-// MINB blocks per SM requested from the register allocator.
+// MINB blocks per SM requested from the register allocator, and the schedule
+// (0: dynamic tasks; 1: static ranges, phase A marching against phase B).
 template <typename T>
 struct KernelSet {
     const void *a, *b, *b_init;
     int W, TY, id;
     size_t smem_b;             // dynamic shared memory of the phase-B kernels
+    int sched;
 };
 
-template <typename T, int VEC, int TY, int MINB>
+// id = 1000 VEC + 10 TY + MINB (dynamic), 1000000 + 1000 VEC + MINB (static).
+template <typename T, int VEC, int TY, int MINB, int SCHED = 0>
 static KernelSet<T> ks_of(int)
 {
-    return {(const void *)k_phase_a<T, VEC, TY, MINB>,
-            (const void *)k_phase_b<T, VEC, TY, MINB, false>,
-            (const void *)k_phase_b<T, VEC, TY, MINB, true>, 32 * VEC, TY,
-            1000 * VEC + 10 * TY + MINB, 0};
+    return {(const void *)k_phase_a<T, VEC, TY, MINB, SCHED>,
+            (const void *)k_phase_b<T, VEC, TY, MINB, false, SCHED>,
+            (const void *)k_phase_b<T, VEC, TY, MINB, true, SCHED>, 32 * VEC, TY,
+            SCHED ? 1000000 + 1000 * VEC + MINB : 1000 * VEC + 10 * TY + MINB, 0, SCHED};
 }
 
 // Phase B staged through shared memory D rows ahead (cp.async); id + 100000 D.
@@ -95,11 +99,11 @@ static KernelSet<T> ks_staged()
         cudaGetLastError();
         attr = true;
     }
-    return {(const void *)k_phase_a<T, VEC, TY, MINB>, b, bi, 32 * VEC, TY,
-            100000 * D + 1000 * VEC + 10 * TY + MINB, smem};
+    return {(const void *)k_phase_a<T, VEC, TY, MINB, 0>, b, bi, 32 * VEC, TY,
+            100000 * D + 1000 * VEC + 10 * TY + MINB, smem, 0};
 }
 
-constexpr int kMaxVariants = 10;
+constexpr int kMaxVariants = 14;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
 static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
@@ -112,10 +116,13 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
         out[n++] = ks_staged<float, 4, 16, 3, 2>();
         out[n++] = ks_of<float, 4, 16, 2>(0);
         out[n++] = ks_of<float, 2, 32, 4>(2);
+        out[n++] = ks_of<float, 4, 32, 2, 1>(0);
+        out[n++] = ks_of<float, 2, 32, 4, 1>(0);
     }
     if (vec8_ok) out[n++] = ks_staged<float, 8, 32, 2, 1>();
     out[n++] = ks_of<float, 1, 32, 4>(4);
     out[n++] = ks_of<float, 1, 16, 4>(5);
+    out[n++] = ks_of<float, 1, 32, 4, 1>(0);
     return n;
 }
 
@@ -126,9 +133,11 @@ static int variants(KernelSet<double> *out, bool vec_ok, bool = false)
         out[n++] = ks_of<double, 2, 32, 2>(0);
         out[n++] = ks_staged<double, 2, 32, 2, 2>();
         out[n++] = ks_of<double, 2, 16, 2>(0);
+        out[n++] = ks_of<double, 2, 32, 2, 1>(0);
     }
     out[n++] = ks_of<double, 1, 32, 3>(4);
     out[n++] = ks_of<double, 1, 16, 3>(5);
+    out[n++] = ks_of<double, 1, 32, 3, 1>(0);
     return n;
 }
 
@@ -265,8 +274,27 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
     h.tiles_x = (h.nth + ks.W - 1) / ks.W;
     h.tiles_y = (h.nz + ks.TY - 1) / ks.TY;
     h.ntiles = (long long)h.tiles_x * h.tiles_y * h.K;
-    run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms);
-    run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b);
+    h.sgroups = 1;
+    if (ks.sched) {
+        // static schedule: both phases get the same warps, so that phase A walks
+        // exactly phase B's ranges backward; groups of >= 4 rows on average
+        int occ_a = 0, occ_b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, ks.a, kThreads, 0) != cudaSuccess)
+            occ_a = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, ks.b, kThreads, ks.smem_b) !=
+            cudaSuccess)
+            occ_b = 1;
+        const long long occ = std::max(1, std::min(occ_a, occ_b));
+        const long long resident = occ * ctx->num_sms * kWarps;
+        const long long L = (long long)h.tiles_x * h.nz;
+        const long long G = std::max(1LL, std::min(resident / h.K, L / 4));
+        const long long warps = std::min(resident, G * h.K);
+        h.sgroups = G;
+        run.grid_a = run.grid_b = (int)((warps + kWarps - 1) / kWarps);
+    } else {
+        run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms);
+        run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b);
+    }
     run.grid_s = stream_grid(h.n * h.K, ctx->num_sms);
 }
 
@@ -275,6 +303,9 @@ static size_t partial_doubles(const PcgRun<T> &run)
 {
     long long m = 2 * run.h.ntiles;
     if (2LL * run.grid_s > m) m = 2LL * run.grid_s;
+    // the static schedule publishes one partial pair per warp
+    if (2LL * kWarps * run.grid_a > m) m = 2LL * kWarps * run.grid_a;
+    if (2LL * kWarps * run.grid_b > m) m = 2LL * kWarps * run.grid_b;
     return (size_t)m;
 }
 

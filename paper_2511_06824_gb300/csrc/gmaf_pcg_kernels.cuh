@@ -236,6 +236,46 @@ __device__ __forceinline__ Task task_of(long long t, int K, int tiles_x, int nz)
     return r;
 }
 
+// Static schedule of a phase (SCHED = 1).  The spatial rows of one condition,
+// L = tiles_x * nz (tile column tx, then row j), are cut into G groups of
+// consecutive rows; item (group g, condition c) = g * K + c goes to warp
+// item mod P (P = warps of the launch), so the warps of one block cover the
+// same rows of several conditions at once.  f(task) is called for each piece of
+// a warp's items (a piece never crosses a tile column); REV walks the items and
+// the pieces of each item in the reverse order.
+template <bool REV, typename F>
+__device__ __forceinline__ void static_pieces(int K, int tiles_x, int nz, int W, long long G,
+                                              long long P, long long gw, F &&f)
+{
+    const long long L = (long long)tiles_x * nz;
+    const long long items = G * K;
+    if (gw >= items) return;
+    const long long mine = (items - 1 - gw) / P + 1;
+    for (long long m = 0; m < mine; ++m) {
+        const long long it = gw + (REV ? mine - 1 - m : m) * P;
+        const long long g = it / K;
+        const int cond = (int)(it - g * K);
+        const long long lo = g * L / G, hi = (g + 1) * L / G;
+        if (!REV) {
+            for (long long a = lo; a < hi;) {
+                const long long tx = a / nz;
+                const long long e = min(hi, (tx + 1) * nz);
+                const Task tk{cond, (int)(tx * W), (int)(a - tx * nz), (int)(e - tx * nz)};
+                f(tk);
+                a = e;
+            }
+        } else {
+            for (long long b = hi; b > lo;) {
+                const long long tx = (b - 1) / nz;
+                const long long a = max(lo, tx * nz);
+                const Task tk{cond, (int)(tx * W), (int)(a - tx * nz), (int)(b - tx * nz)};
+                f(tk);
+                b = a;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int wrap_col(int c, int n)
 {
     int r = c % n;
@@ -282,12 +322,19 @@ __device__ __forceinline__ bool reduce_tasks(const double *partials, unsigned nt
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
+    // each thread adds the partials of tasks threadIdx.x, + blockDim.x, ... in
+    // that order; the unrolled loop keeps several L2 loads in flight
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+#pragma unroll 4
+    for (unsigned t = threadIdx.x; t < ntasks; t += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&partials[(size_t)t * NV + q]);
+    }
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        double s = 0.0;
-        for (unsigned t = threadIdx.x; t < ntasks; t += blockDim.x)
-            s += __ldcg(&partials[(size_t)t * NV + q]);
-        s = warp_sum_d(s);
+        const double s = warp_sum_d(acc[q]);
         if (lane == 0) red[q][wid] = s;
     }
     __syncthreads();
@@ -317,9 +364,11 @@ struct RowA {
     T hz, huo, he;
 };
 
-// One task of phase A; returns the lane's share of the task's u.v.
-template <typename T, int VEC, int TY>
-__device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, int k, bool first,
+// One task of phase A; returns the lane's share of the task's u.v.  UP marches
+// the rows from the top of the task down to its bottom (jend -> j0): the stencil
+// is symmetric in z, so only the roles of the two aN couplings swap.
+template <typename T, int VEC, bool UP>
+__device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk, int k, bool first,
                                              T alpha_prev, T beta, T *ub, T *ab, int lane)
 {
     constexpr int W = 32 * VEC;
@@ -328,7 +377,6 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, in
     const T *uo_base = d.u[(k + 1) & 1];
     T *un_base = d.u[k & 1];
         RowAcc<T> acc;
-        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, nz);
         const size_t off = (size_t)tk.cond * (size_t)n;
         const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
         const T *z = d.z + off;
@@ -343,9 +391,13 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, in
         const bool owned = c0 < nth;
         const int g0 = wrap_col(c0, nth);
         const int sown = 4 + lane * VEC;
-        // halo: lane 0 -> column i0 - 1 (slot 3), lane 1 -> column i0 + W (slot W + 4)
+        // halo: lane 0 -> column i0 - 1 (slot 3), lane 1 -> column i0 + W (slot W + 4);
+        // branch-free: every lane loads (lanes 2..31 at lane 1's column) and lanes
+        // without a halo column store into the spare slot W + 7
         const int hg = wrap_col(lane == 0 ? tk.i0 - 1 : tk.i0 + W, nth);
         const int hslot = lane == 0 ? 3 : W + 4;
+        const int hslot_u = lane < 2 ? hslot : W + 7;
+        const int hslot_a = lane == 0 ? hslot : W + 7;
 
         auto load_row = [&](int jr, RowA<T, VEC> &R) {
             if (jr < 0 || jr >= nz) {
@@ -376,13 +428,10 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, in
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) R.D[q] = R.e[q] = R.p[q] = T(0);
             }
-            R.hz = R.huo = R.he = T(0);
-            if (lane < 2) {
-                const size_t qh = (size_t)jr * nth + hg;
-                R.hz = __ldg(z + qh);
-                if (!first) R.huo = __ldg(uo + qh);
-                if (lane == 0) R.he = __ldg(aE + qh);
-            }
+            const size_t qh = (size_t)jr * nth + hg;
+            R.hz = __ldg(z + qh);
+            R.huo = first ? T(0) : __ldg(uo + qh);
+            R.he = __ldg(aE + qh);
         };
 
         T u_m1[VEC], u_m2[VEC], uo_m1[VEC], D_m1[VEC], e_m1[VEC], n_m1[VEC], n_m2[VEC], p_m1[VEC];
@@ -390,16 +439,20 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, in
         for (int q = 0; q < VEC; ++q)
             u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = T(0);
         RowA<T, VEC> nx;
-        load_row(tk.j0 - 1, nx);
-        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+        constexpr int step = UP ? -1 : 1;
+        const int jfirst = UP ? tk.jend : tk.j0 - 1;
+        const int jlast = UP ? tk.j0 - 1 : tk.jend;
+        load_row(jfirst, nx);
+        for (int jr = jfirst; UP ? jr >= jlast : jr <= jlast; jr += step) {
             const RowA<T, VEC> cur = nx;
-            if (jr + 1 <= tk.jend) load_row(jr + 1, nx);
+            if (jr != jlast) load_row(jr + step, nx);
             T u[VEC];
 #pragma unroll
             for (int q = 0; q < VEC; ++q) u[q] = first ? cur.z[q] : cur.z[q] + beta * cur.uo[q];
             const T hu = first ? cur.hz : cur.hz + beta * cur.huo;
-            // output row jo = jr - 1: its u row and aE row are in the shared buffers
-            const int jo = jr - 1;
+            // output row jo (the previous step's row): its u row and aE row are in
+            // the shared buffers; u_m2 is the row beyond jo, u the row before it
+            const int jo = jr - step;
             if (jo >= tk.j0 && jo < tk.jend) {
                 T vout[VEC];
                 T rowsum = T(0);
@@ -409,8 +462,12 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, in
                     const T uE = (q < VEC - 1) ? u_m1[q + 1] : ub[s + 1];
                     const T uW = (q > 0) ? u_m1[q - 1] : ub[s - 1];
                     const T aW = (q > 0) ? e_m1[q - 1] : ab[s - 1];
-                    vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
-                              n_m2[q] * u_m2[q];
+                    if (UP)   // n_m1 = aN(jo) couples jo + 1 (u_m2); cur.n = aN(jo - 1) couples u
+                        vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u_m2[q] -
+                                  cur.n[q] * u[q];
+                    else      // n_m1 = aN(jo) couples jo + 1 (u); n_m2 = aN(jo - 1) couples u_m2
+                        vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
+                                  n_m2[q] * u_m2[q];
                     rowsum += u_m1[q] * vout[q];
                 }
                 if (owned) {
@@ -429,10 +486,8 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, unsigned t, in
             __syncwarp();
             Vec<T, VEC>::st(ub + sown, u);
             Vec<T, VEC>::st(ab + sown, cur.e);
-            if (lane < 2) {
-                ub[hslot] = hu;
-                if (lane == 0) ab[hslot] = cur.he;
-            }
+            ub[hslot_u] = hu;
+            ab[hslot_a] = cur.he;
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
@@ -461,7 +516,10 @@ __device__ __forceinline__ void finish_a(Scalars *sc, double uv)
     }
 }
 
-template <typename T, int VEC, int TY, int MINB>
+// SCHED 0: dynamic tasks of TY rows, marched downward.  SCHED 1: the static
+// schedule, marched upward, mirroring phase B (which marches downward), so each
+// phase starts on the rows the other touched last and finds them in L2.
+template <typename T, int VEC, int TY, int MINB, int SCHED>
 __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__restrict__ dp)
 {
     constexpr int W = 32 * VEC;
@@ -487,12 +545,26 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
     __syncthreads();
     if (s_done) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const unsigned ntasks = (unsigned)d.ntiles;
-    for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
-         t = next_task(&sc->task_ctr[0], lane)) {
-        const double val[1] = {run_task_a<T, VEC, TY>(d, t, s_k, s_first != 0, (T)s_alpha,
-                                                       (T)s_beta, su[wp], sa[wp], lane)};
-        publish_task<1>(val, d.partials, t, lane);
+    unsigned ntasks;
+    if (SCHED == 0) {
+        ntasks = (unsigned)d.ntiles;
+        for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
+             t = next_task(&sc->task_ctr[0], lane)) {
+            const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+            const double val[1] = {run_task_a<T, VEC, false>(d, tk, s_k, s_first != 0, (T)s_alpha,
+                                                              (T)s_beta, su[wp], sa[wp], lane)};
+            publish_task<1>(val, d.partials, t, lane);
+        }
+    } else {
+        ntasks = gridDim.x * kWarps;
+        const unsigned gw = blockIdx.x * kWarps + wp;
+        double v = 0.0;
+        static_pieces<true>(d.K, d.tiles_x, d.nz, W, d.sgroups, ntasks, gw, [&](const Task &tk) {
+            v += run_task_a<T, VEC, true>(d, tk, s_k, s_first != 0, (T)s_alpha, (T)s_beta, su[wp],
+                                          sa[wp], lane);
+        });
+        const double val[1] = {v};
+        publish_task<1>(val, d.partials, gw, lane);
     }
     double tot[1];
     if (reduce_tasks<1>(d.partials, ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
@@ -517,11 +589,19 @@ struct RowB {
 };
 
 // One task of phase B; writes the lane's shares of the task's r.z and r.r.
-template <typename T, int VEC, int TY, bool INIT>
-__device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int k, T alpha,
+// One task of phase B; writes the lane's shares of the task's r.z and r.r.
+// One body serves every task (a second, specialised copy of this unrolled body
+// measured slower: the kernel is sensitive to its code size).  In FP32 the halo
+// work is branch-free: every lane issues the halo loads, lanes 4..31 at lane
+// 3's column (same address, no extra traffic) and into a spare shared slot.  In
+// FP64, bound by the FP64 pipe, only the lanes that own a halo column do it.
+template <typename T, int VEC, bool INIT>
+__device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, int k, T alpha,
                                            T *yb, T *wb, T *ab, int lane, double (&out)[2])
 {
     constexpr int W = 32 * VEC;
+    constexpr int kSpare = W + 7;      // shared slot written by lanes without a halo column
+    constexpr bool BF = sizeof(T) == 4;
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
     const T omega = d.omega, c1 = d.c1;
@@ -529,7 +609,6 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
     const T *ro_base = d.r[k & 1];
     T *rn_base = d.r[(k + 1) & 1];
         RowAcc<T> arz, arr;
-        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, nz);
         const size_t off = (size_t)tk.cond * (size_t)n;
         const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
         const T *ro = ro_base + off;
@@ -544,15 +623,18 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
         const int g0 = wrap_col(c0, nth);
         const int sown = 4 + lane * VEC;
         // halo: lanes 0..3 -> columns i0-2, i0-1 (slots 2, 3), i0+W, i0+W+1 (slots W+4, W+5)
-        const int hoff = lane < 2 ? lane - 2 : W + (lane - 2);
+        const int hl = lane < 4 ? lane : 3;
+        const int hoff = hl < 2 ? hl - 2 : W + (hl - 2);
         const int hg = wrap_col(tk.i0 + hoff, nth);
-        const int hslot = lane < 2 ? lane + 2 : W + 2 + lane;
+        const int hs = hl < 2 ? hl + 2 : W + 2 + hl;          // the halo column's slot
+        const int hslot_y = lane < 4 ? hs : kSpare;            // y, aE of lanes 0..3
+        const int hslot_w = (lane == 1 || lane == 2) ? hs : kSpare;   // w of lanes 1, 2
 
         auto load_row = [&](int jr, RowB<T, VEC> &R) {
-            R.hr = R.hv = R.hd = R.he = R.hn = T(0);
             if (jr < 0 || jr >= nz) {
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) R.r[q] = R.v[q] = R.dI[q] = R.e[q] = R.n[q] = T(0);
+                R.hr = R.hv = R.hd = R.he = R.hn = T(0);
                 return;
             }
             const size_t q0 = (size_t)jr * nth + g0;
@@ -566,7 +648,8 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
             Vec<T, VEC>::ld(invD + q0, R.dI);
             Vec<T, VEC>::ld(aE + q0, R.e);
             Vec<T, VEC>::ld(aN + q0, R.n);
-            if (lane < 4) {
+            R.hr = R.hv = R.hd = R.he = R.hn = T(0);
+            if (BF || lane < 4) {
                 const size_t qh = (size_t)jr * nth + hg;
                 R.hr = __ldg(ro + qh);
                 if (!INIT) R.hv = __ldg(vv + qh);
@@ -579,7 +662,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
         T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
-        T hy_m1 = T(0), hn_m1 = T(0);
+        T hy_m1 = T(0), hn_m1 = T(0), he_m1 = T(0);
         RowB<T, VEC> nx;
         load_row(tk.j0 - 1, nx);
         for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
@@ -595,10 +678,15 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
             const T hy = (INIT ? cur.hr : cur.hr - alpha * cur.hv) * cur.hd;
             Vec<T, VEC>::st(yb + sown, y);
             Vec<T, VEC>::st(ab + sown, cur.e);
-            if (lane < 4) {
-                yb[hslot] = hy;
-                ab[hslot] = cur.he;
+            if (BF || lane < 4) {
+                yb[hslot_y] = hy;
+                ab[hslot_y] = cur.he;
             }
+            // FP32: aE(jr - 1, n_theta - 1), the wrapped west coupling of column 0 in
+            // the second pass, from lane 1 (column i0 - 1, which is n_theta - 1 when
+            // i0 = 0); FP64 loads it where it is needed
+            T aw_wrap = T(0);
+            if (BF) aw_wrap = __shfl_sync(0xffffffffu, he_m1, 1);
             __syncwarp();
             // first ASSOR pass on row jr: w = y + omega D^-1 (lower couplings) y
             T w[VEC];
@@ -616,12 +704,12 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
                     if (gi == nth - 1) sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);  // east, wrapped
                     w[q] = y[q] + omega * cur.dI[q] * sum;
                 }
-                if (lane == 1 || lane == 2) {
-                    const int s = hslot;
+                // halo w (used for lanes 1, 2; in FP32 the others compute and discard it)
+                if (BF || lane == 1 || lane == 2) {
                     T sum = T(0);
                     if (jr > 0) sum += hn_m1 * hy_m1;
-                    if (hg > 0) sum += ab[s - 1] * yb[s - 1];
-                    if (hg == nth - 1) sum += cur.he * yb[s + 1];
+                    if (hg > 0) sum += ab[hs - 1] * yb[hs - 1];
+                    if (hg == nth - 1) sum += cur.he * yb[hs + 1];
                     hw = hy + omega * cur.hd * sum;
                 }
             }
@@ -638,7 +726,8 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
                         if (jo < nz - 1) sum += n_m1[q] * w[q];                                          // north
                         if (gi < nth - 1) sum += e_m1[q] * ((q < VEC - 1) ? w_m1[q + 1] : wb[s + 1]);    // east
                         if (gi == 0)                                                                     // west, wrapped
-                            sum += __ldg(aE + (size_t)jo * nth + nth - 1) * ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
+                            sum += (BF ? aw_wrap : __ldg(aE + (size_t)jo * nth + nth - 1)) *
+                                   ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
                         zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
                     } else {
                         zz[q] = y_m1[q];
@@ -657,7 +746,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
             __syncwarp();
             if (assor) {
                 Vec<T, VEC>::st(wb + sown, w);
-                if (lane == 1 || lane == 2) wb[hslot] = hw;
+                if (BF || lane == 1 || lane == 2) wb[hslot_w] = hw;
             }
             __syncwarp();
 #pragma unroll
@@ -671,6 +760,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, unsigned t, int 
             }
             hy_m1 = hy;
             hn_m1 = cur.hn;
+            he_m1 = cur.he;
         }
     out[0] = arz.value();
     out[1] = arr.value();
@@ -727,7 +817,9 @@ __device__ __forceinline__ int finish_b(Scalars *sc, double rz, double rr, int k
     return done;
 }
 
-template <typename T, int VEC, int TY, int MINB, bool INIT>
+// SCHED 0: dynamic tasks of TY rows, claimed in the reverse of phase A's order.
+// SCHED 1: the static schedule in forward order (phase A walks it backward).
+template <typename T, int VEC, int TY, int MINB, bool INIT, int SCHED>
 __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__restrict__ dp)
 {
     constexpr int W = 32 * VEC;
@@ -747,12 +839,30 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__
     __syncthreads();
     if (s_done) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const unsigned ntasks = (unsigned)d.ntiles;
-    for (unsigned t = next_task(&sc->task_ctr[1], lane); t < ntasks;
-         t = next_task(&sc->task_ctr[1], lane)) {
-        double val[2];
-        run_task_b<T, VEC, TY, INIT>(d, t, s_k, (T)s_alpha, sy[wp], sw[wp], sa[wp], lane, val);
-        publish_task<2>(val, d.partials, t, lane);
+    unsigned ntasks;
+    if (SCHED == 0) {
+        ntasks = (unsigned)d.ntiles;
+        // tasks are claimed in the reverse of phase A's order; partials stay
+        // indexed by task, so the totals do not depend on the order
+        for (unsigned c = next_task(&sc->task_ctr[1], lane); c < ntasks;
+             c = next_task(&sc->task_ctr[1], lane)) {
+            const unsigned t = ntasks - 1u - c;
+            const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+            double val[2];
+            run_task_b<T, VEC, INIT>(d, tk, s_k, (T)s_alpha, sy[wp], sw[wp], sa[wp], lane, val);
+            publish_task<2>(val, d.partials, t, lane);
+        }
+    } else {
+        ntasks = gridDim.x * kWarps;
+        const unsigned gw = blockIdx.x * kWarps + wp;
+        double v[2] = {0.0, 0.0};
+        static_pieces<false>(d.K, d.tiles_x, d.nz, W, d.sgroups, ntasks, gw, [&](const Task &tk) {
+            double val[2];
+            run_task_b<T, VEC, INIT>(d, tk, s_k, (T)s_alpha, sy[wp], sw[wp], sa[wp], lane, val);
+            v[0] += val[0];
+            v[1] += val[1];
+        });
+        publish_task<2>(v, d.partials, gw, lane);
     }
     double tot[2];
     if (reduce_tasks<2>(d.partials, ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
@@ -966,9 +1076,12 @@ struct RingB {
     __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
 };
 
-// EDGE = false: the strip and its halo touch neither theta edge (2 <= i0 and
-// i0 + W + 2 <= n_theta), so no periodic-wrap rule can apply and the tests are
-// compiled out.
+// Only lanes 0..3 issue the halo copies (copies of one word from many lanes into
+// one shared slot serialise).  FP32: one body for every task, branch-free halo
+// arithmetic as in run_task_b (reading lane 3's column).  FP64 (bound by the
+// FP64 pipe, where it measured faster): interior tasks take a second body
+// (EDGE = false: the strip and its halo touch neither theta edge, 2 <= i0 and
+// i0 + W + 2 <= n_theta), with the periodic-wrap tests compiled out.
 template <typename T, int VEC, int TY, bool INIT, int D, bool EDGE>
 __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Task &tk, int k,
                                                   T alpha, T *ring, T *yb, T *wb, int lane,
@@ -976,6 +1089,8 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
 {
     constexpr int W = 32 * VEC;
     constexpr int NB = W + 8, NF = 5, SLOT = NF * NB;
+    constexpr int kSpare = W + 7;
+    constexpr bool BF = sizeof(T) == 4;
     constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
     static_assert(VEC % CH == 0, "whole 16-byte chunks per lane");
     const int nth = d.nth, nz = d.nz;
@@ -989,15 +1104,18 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     const bool owned = c0 < nth;
     const int g0 = EDGE ? wrap_col(c0, nth) : c0;
     const int sown = 4 + lane * VEC;
-    const int hoff = lane < 2 ? lane - 2 : W + (lane - 2);
+    const int hl = lane < 4 ? lane : 3;
+    const int hoff = hl < 2 ? hl - 2 : W + (hl - 2);
     const int hg = EDGE ? wrap_col(tk.i0 + hoff, nth) : tk.i0 + hoff;
-    const int hslot = lane < 2 ? lane + 2 : W + 2 + lane;
+    const int hs = hl < 2 ? hl + 2 : W + 2 + hl;
+    const int hslot_y = lane < 4 ? hs : kSpare;
+    const int hslot_w = (lane == 1 || lane == 2) ? hs : kSpare;
+    const T *aE = d.aE + coff;
     // row pointers at row j0 - 1 (own columns / halo column); advanced by n_theta per row
     const long long row0 = (long long)(tk.j0 - 1) * nth;
     const T *src[NF] = {d.r[k & 1] + off, d.v + off, d.invD + coff, d.aE + coff, d.aN + coff};
     T *rn = d.r[(k + 1) & 1] + off + (long long)tk.j0 * nth + g0;
     T *zo = d.z + off + (long long)tk.j0 * nth + g0;
-    const T *aE = d.aE + coff;
 
     auto issue = [&](int jr) {
         if (jr >= 0 && jr < nz && jr <= tk.jend) {
@@ -1013,7 +1131,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     if (INIT && f == 1) continue;
-                    cp_async_small<sizeof(T)>(slot + f * NB + hslot, src[f] + rq + hg);
+                    cp_async_small<sizeof(T)>(slot + f * NB + hs, src[f] + rq + hg);
                 }
             }
         }
@@ -1023,7 +1141,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
-    T hy_m1 = T(0), hn_m1 = T(0);
+    T hy_m1 = T(0), hn_m1 = T(0), he_m1 = T(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
     for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
@@ -1046,11 +1164,11 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
                 r1[q] = INIT ? rv[q] : rv[q] - alpha * vx[q];
                 y[q] = r1[q] * dI[q];
             }
-            if (lane < 4) {
-                const T hr = INIT ? cur[hslot] : cur[hslot] - alpha * cur[NB + hslot];
-                hd = cur[2 * NB + hslot];
-                he = cur[3 * NB + hslot];
-                hn = cur[4 * NB + hslot];
+            if (BF || lane < 4) {
+                const T hr = INIT ? cur[hs] : cur[hs] - alpha * cur[NB + hs];
+                hd = cur[2 * NB + hs];
+                he = cur[3 * NB + hs];
+                hn = cur[4 * NB + hs];
                 hy = hr * hd;
             }
         } else {
@@ -1058,7 +1176,11 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
             for (int q = 0; q < VEC; ++q) r1[q] = y[q] = dI[q] = ev[q] = nv[q] = T(0);
         }
         Vec<T, VEC>::st(yb + sown, y);
-        if (lane < 4) yb[hslot] = hy;
+        if (BF || lane < 4) yb[hslot_y] = hy;
+        // FP32: aE(jr - 1, n_theta - 1) from lane 1 (column i0 - 1): wrapped west
+        // coupling of column 0; FP64 loads it where it is needed
+        T aw_wrap = T(0);
+        if (BF) aw_wrap = __shfl_sync(0xffffffffu, he_m1, 1);
         __syncwarp();
         T w[VEC];
         T hw = T(0);
@@ -1069,28 +1191,18 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
             const bool south = jr > 0;
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-                const int s = sown + q;
+                const int s = sown + q, gi = g0 + q;
                 T sum = south ? n_m1[q] * y_m1[q] : T(0);
                 const T aW = (q > 0) ? ev[q - 1] : ab[s - 1];
                 const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
-                if (!EDGE) {
-                    sum += aW * yW;
-                } else {
-                    const int gi = g0 + q;
-                    if (gi > 0) sum += aW * yW;
-                    if (gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
-                }
+                if (!EDGE || gi > 0) sum += aW * yW;
+                if (EDGE && gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
                 w[q] = y[q] + omega * dI[q] * sum;
             }
-            if (lane == 1 || lane == 2) {
-                const int s = hslot;
+            if (BF || lane == 1 || lane == 2) {
                 T sum = south ? hn_m1 * hy_m1 : T(0);
-                if (!EDGE) {
-                    sum += ab[s - 1] * yb[s - 1];
-                } else {
-                    if (hg > 0) sum += ab[s - 1] * yb[s - 1];
-                    if (hg == nth - 1) sum += he * yb[s + 1];
-                }
+                if (!EDGE || hg > 0) sum += ab[hs - 1] * yb[hs - 1];
+                if (EDGE && hg == nth - 1) sum += he * yb[hs + 1];
                 hw = hy + omega * hd * sum;
             }
         }
@@ -1102,17 +1214,13 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
                 if (assor) {
-                    const int s = sown + q;
+                    const int s = sown + q, gi = g0 + q;
                     T sum = north ? n_m1[q] * w[q] : T(0);
                     const T wE = (q < VEC - 1) ? w_m1[q + 1] : wb[s + 1];
-                    if (!EDGE) {
-                        sum += e_m1[q] * wE;
-                    } else {
-                        const int gi = g0 + q;
-                        if (gi < nth - 1) sum += e_m1[q] * wE;
-                        if (gi == 0)
-                            sum += __ldg(aE + (size_t)jo * nth + nth - 1) * ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
-                    }
+                    if (!EDGE || gi < nth - 1) sum += e_m1[q] * wE;
+                    if (EDGE && gi == 0)
+                        sum += (BF ? aw_wrap : __ldg(aE + (size_t)jo * nth + nth - 1)) *
+                               ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
                     zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
                 } else {
                     zz[q] = y_m1[q];
@@ -1132,7 +1240,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         __syncwarp();
         if (assor) {
             Vec<T, VEC>::st(wb + sown, w);
-            if (lane == 1 || lane == 2) wb[hslot] = hw;
+            if (BF || lane == 1 || lane == 2) wb[hslot_w] = hw;
         }
         __syncwarp();
 #pragma unroll
@@ -1146,6 +1254,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         }
         hy_m1 = hy;
         hn_m1 = hn;
+        he_m1 = he;
     }
     cp_wait<0>();
     __syncwarp();
@@ -1176,11 +1285,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc
     T *wb = yb + R::NB;
     const unsigned ntasks = (unsigned)d.ntiles;
     constexpr int W = 32 * VEC;
-    for (unsigned t = next_task(&sc->task_ctr[1], lane); t < ntasks;
-         t = next_task(&sc->task_ctr[1], lane)) {
+    for (unsigned c = next_task(&sc->task_ctr[1], lane); c < ntasks;
+         c = next_task(&sc->task_ctr[1], lane)) {
+        const unsigned t = ntasks - 1u - c;    // reverse of phase A's order (L2 reuse)
         double val[2];
         const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
-        if (tk.i0 >= 2 && tk.i0 + W + 2 <= d.nth)
+        if (sizeof(T) == 8 && tk.i0 >= 2 && tk.i0 + W + 2 <= d.nth)
             run_task_b_staged<T, VEC, TY, INIT, D, false>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
         else
             run_task_b_staged<T, VEC, TY, INIT, D, true>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
@@ -1300,7 +1410,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         beta = __shfl_sync(0xffffffffu, beta, 0);
         double val[1] = {0.0};
         if (!done)
-            val[0] = run_task_a<T, VEC, TY>(d, t - m.task_off[g], k, first != 0, (T)alpha, (T)beta,
+            val[0] = run_task_a<T, VEC, false>(d, task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz),
+                                               k, first != 0, (T)alpha, (T)beta,
                                             su[wp], sa[wp], lane);
         publish_task<1>(val, m.partials, t, lane);
     }
@@ -1336,8 +1447,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
     __syncthreads();
     if (s_idle) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    for (unsigned t = next_task(&m.msc->task_ctr[1], lane); t < m.total_tasks;
-         t = next_task(&m.msc->task_ctr[1], lane)) {
+    for (unsigned c = next_task(&m.msc->task_ctr[1], lane); c < m.total_tasks;
+         c = next_task(&m.msc->task_ctr[1], lane)) {
+        const unsigned t = m.total_tasks - 1u - c;    // reverse of phase A's order (L2 reuse)
         const int g = group_of(m.task_off, m.ngroups, t);
         const PcgDesc<T> &d = m.groups[g];
         int done = 0, k = 0;
@@ -1352,7 +1464,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
         alpha = __shfl_sync(0xffffffffu, alpha, 0);
         double val[2] = {0.0, 0.0};
         if (!done)
-            run_task_b<T, VEC, TY, false>(d, t - m.task_off[g], k, (T)alpha, sy[wp], sw[wp], sa[wp],
+            run_task_b<T, VEC, false>(d, task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz), k,
+                                      (T)alpha, sy[wp], sw[wp], sa[wp],
                                           lane, val);
         publish_task<2>(val, m.partials, t, lane);
     }

@@ -233,7 +233,7 @@ static int start_inner(gmaf_server *sv, Request *r, double true_rel)
     k_reset<<<1, 32, 0, s>>>(r->sc_in, 0);
     k_init_r<float><<<r->grid_s, kThreads, 0, s>>>(r->d_desc);
     const int gb = (int)std::min<long long>((r->ntasks + kWarps - 1) / kWarps, (long long)sv->num_sms * kSvMinB);
-    k_phase_b<float, kSvVec, kSvTY, kSvMinB, true><<<gb, kThreads, 0, s>>>(r->d_desc);
+    k_phase_b<float, kSvVec, kSvTY, kSvMinB, true, 0><<<gb, kThreads, 0, s>>>(r->d_desc);
     r->outer += 1;
     sv->dirty = true;
     return cuda_status(cudaGetLastError());

@@ -226,6 +226,56 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
     assert np.array_equal(host(p), outs[0])
 
 
+# dynamic tasks (ids 1000 VEC + 10 TY + MINB) and the static schedule with phase A
+# marching against phase B (ids 1000000 + 1000 VEC + MINB); float VEC > 1 kernels
+# need n_theta % 4 == 0, double ones an even n_theta
+@pytest.mark.parametrize("precision,variant,nth,nz,K", [
+    (1, 4322, 132, 45, 9), (1, 1004002, 132, 45, 9), (1, 1002004, 260, 33, 4),
+    (1, 1001004, 131, 7, 3), (0, 2322, 130, 45, 9), (0, 1002002, 130, 45, 9),
+    (0, 1001003, 131, 7, 3), (0, 1001003, 3, 2, 1),
+])
+def test_each_schedule_matches_oracle(g, monkeypatch, precision, variant, nth, nz, K):
+    monkeypatch.setenv("GMAF_VARIANT", str(variant))
+    c = g.Context()
+    try:
+        conds = states(K, seed=nth + K)
+        p, it, rel, po, ito, _ = solve_both(g, c.handle, nth, nz, tex_dimples(), conds,
+                                            precision=precision)
+        info = g.gmaf_last_solve_info(c.handle)
+    finally:
+        c.close()
+    assert info["kernel_variant"] == variant
+    assert rel <= 1e-9
+    if precision == 0:
+        assert abs(it - ito) <= 2, (it, ito)
+        assert rel_l2(p, po) <= 1e-9
+    else:
+        assert rel_l2(p, po) <= 1e-6
+
+
+@pytest.mark.parametrize("variant", [1002002, 1001003])
+def test_static_schedule_is_deterministic_and_graph_matches_host_loop(g, monkeypatch, variant):
+    """The static schedule sums one partial per warp in warp order: for a fixed
+    launch shape the graph-driven and host-driven solves agree bitwise."""
+    conds = states(9, seed=12)
+    nth, nz = 150, 50
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
+    args = [dev(D), dev(aE), dev(aN), dev(S)]
+    n = 9 * nth * nz
+    monkeypatch.setenv("GMAF_VARIANT", str(variant))
+    outs = []
+    for no_graph in ("0", "0", "1"):
+        if no_graph == "1":
+            monkeypatch.setenv("GMAF_NO_GRAPH", "1")
+        c = g.Context()
+        p = zeros(n)
+        g.gmaf_solve_joint(c.handle, nth, nz, 9, *args, p)
+        assert g.gmaf_last_solve_info(c.handle)["kernel_variant"] == variant
+        c.close()
+        outs.append(host(p))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
 def test_hbm_budget_is_enforced(g):
     c = g.Context(hbm_budget_bytes=1 << 20)
     n = 9 * 256 * 128
