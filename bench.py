@@ -155,18 +155,18 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, precision: str, kernel: str):
+def ncu_traffic(workload: str, precision: str, variant: int, kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    current kernel source and kernel variant (else None)."""
     path = os.path.join(ROOT, "profiles", "pcg_phases_dram.txt")
     if not os.path.exists(path):
         return None
     want = source_hash()
     for line in open(path):
         f = line.split()
-        if len(f) >= 6 and f[0] == "traffic" and f[1] == want and f[2] == workload and \
-                f[3] == precision and f[4] == kernel:
-            return float(f[5])
+        if len(f) >= 7 and f[0] == "traffic" and f[1] == want and f[2] == workload and \
+                f[3] == precision and f[4] == str(variant) and f[5] == kernel:
+            return float(f[6])
     return None
 
 
@@ -297,7 +297,7 @@ def run_ours(args):
     d = phases[dom]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["achieved_gbs"], 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(d["frac"], 4),
-                "traffic": ncu_traffic(args.workload, args.precision, dom),
+                "traffic": ncu_traffic(args.workload, args.precision, timed.info["kernel_variant"], dom),
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json copy bandwidth)",
                 "alg_bytes_per_launch": bpd[dom] * w.dof}
 
