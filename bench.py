@@ -58,10 +58,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "dynamics", "serving"], default="step",
+    ap.add_argument("--mode", choices=["step", "dynamics", "serving", "strategies"], default="step",
                     help="step: Picard steps of the joint batch (default); dynamics: the "
                          "multi-period march on the textured 1024x512 gap; serving: a Poisson "
-                         "stream of uneven requests, batched server vs sequential FP64")
+                         "stream of uneven requests, batched server vs sequential FP64; "
+                         "strategies: synchronized vs asynchronized convergence criterion (FP64)")
     ap.add_argument("--requests", type=int, default=24, help="requests in the stream (serving)")
     ap.add_argument("--rate", type=float, default=20.0, help="arrival rate [1/s] (serving)")
     ap.add_argument("--budget-gb", type=float, default=24.0, help="server HBM budget (serving)")
@@ -471,6 +472,50 @@ def run_dynamics(args):
     print(json.dumps(out), flush=True)
 
 
+def run_strategies(args):
+    """Synchronized (Eq. 3.9) against asynchronized (Eq. 3.10) convergence criterion
+    on the joint solve of one Picard step, FP64, as in the paper's Sec. 4.2 / Table 3:
+    iterations (the asynchronized count averaged over the conditions, and its maximum),
+    solve time and time per iteration.  Both run in one persistent launch per CG phase;
+    under the asynchronized criterion converged conditions drop out on the device."""
+    import torch
+    from paper_2511_06824_gb300 import build as gbuild
+    from paper_2511_06824_gb300 import gmaf, inputs
+    gbuild.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = inputs.make(args.workload, args.seed)
+    out = {"metric": "joint PCG solve time, synchronized vs asynchronized criterion",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "joint_dof": w.dof, "omega": w.omega, "eps": w.eps,
+                      "precond": "ASSOR-II"}}
+    with gmaf.Context() as c:
+        for name, crit in (("synchronized", 0), ("asynchronized", 1)):
+            opts = gmaf.solver_opts(precond=1, omega=w.omega, eps=w.eps, precision=0, criterion=crit)
+            step = lambda: gmaf.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state,
+                                                 w.state[:4], 2.7777777777777778e-4, np.zeros(4),
+                                                 w.d_e, w.d_edot, opts)
+            step()                                    # tuning, allocation
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = step()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            info = gmaf.gmaf_last_solve_info(c.handle)
+            out[name] = {"s": dt, "iterations": info["iterations"],
+                         "avg_iterations_per_condition": info["iterations_sum"] / w.n_cond,
+                         "ms_per_iteration": 1e3 * dt / max(info["iterations"], 1),
+                         "true_rel_residual": info["true_rel_residual"], "status": r["status"],
+                         "loads": [float(x) for x in r["loads"]]}
+    sy, asy = out["synchronized"], out["asynchronized"]
+    out["value"] = asy["s"] / sy["s"]
+    out["value_is"] = "asynchronized time / synchronized time"
+    out["iteration_ratio_avg"] = asy["avg_iterations_per_condition"] / max(sy["iterations"], 1)
+    out["ms_per_iteration_ratio"] = asy["ms_per_iteration"] / sy["ms_per_iteration"]
+    ld = np.array(asy["loads"]) - np.array(sy["loads"])
+    out["max_load_difference"] = float(np.max(np.abs(ld) / np.maximum(np.abs(sy["loads"]), 1e-3 * np.linalg.norm(sy["loads"]))))
+    print(json.dumps(out), flush=True)
+
+
 def run_serving(args):
     """Poisson stream of Picard-step requests, grids uniform over 256x128 .. 2048x1024,
     half of them textured: the continuous-batching mixed-precision server against the
@@ -517,6 +562,8 @@ def main():
         run_dynamics(args)
     elif args.mode == "serving":
         run_serving(args)
+    elif args.mode == "strategies":
+        run_strategies(args)
     else:
         run_ours(args)
 

@@ -79,7 +79,7 @@ typedef struct {
 typedef struct { double e[4], edot[4]; } gmaf_state;
 
 /* precond: 0 Jacobi (Eq. 2.8), 1 ASSOR-II (Eq. 3.4).  omega in (0, 2).
- * eps: synchronized criterion ||A_G p_G - S_G||_2 / ||S_G||_2 <= eps (Eq. 3.9).
+ * eps: tolerance of the convergence criterion below.
  * max_iter: PCG iteration budget (inner iterations in mixed precision).
  * precision: 0 FP64 throughout; 1 mixed - FP32 stencil, preconditioner and
  *   vector updates with dot products accumulated to FP64 accuracy, inside an
@@ -91,6 +91,14 @@ typedef struct {
     int32_t max_iter;
     int32_t precision;
     int32_t zero_init;
+    int32_t criterion;  /* 0 synchronized (Sec. 3.3, Eq. 3.9): one PCG on the joint
+                           system with global scalars, stopped when
+                           ||A_G p_G - S_G||_2 / ||S_G||_2 <= eps.
+                           1 asynchronized (Eq. 3.10): every condition k is its own
+                           PCG with its own scalars, stopped when
+                           ||A_k p_k - S_k||_2 / ||S_k||_2 <= eps; converged
+                           conditions drop out on the device.  FP64 only
+                           (precision 0); GMAF_INVALID_ARG otherwise. */
 } gmaf_solver_opts;
 
 /* Details of the last solve on a context (filled by gmaf_solve_joint and
@@ -106,6 +114,10 @@ typedef struct {
                                   lane, rows per task, blocks per SM); chosen per problem
                                   shape by the autotuner on the first solve of that shape */
     int32_t tasks;             /* strip x row-block x condition tasks per PCG phase       */
+    int32_t iterations_sum;    /* PCG iterations summed over the conditions: n_cond x
+                                  iterations under the synchronized criterion, the sum of
+                                  the per-condition counts under the asynchronized one
+                                  (iterations is then the largest of them)              */
 } gmaf_solve_info;
 
 typedef struct gmaf_ctx gmaf_ctx;
@@ -199,7 +211,8 @@ int gmaf_phase_timing(const gmaf_ctx *ctx, double ms_out[4], int64_t launches_ou
  * all of the GPU's memory and offers plug-ins no allocation hook, or a
  * real-time co-simulation loop that cannot accept the latency, or the possible
  * failure, of an allocation in the middle of a time step.  It computes what
- * gmaf_solve_joint computes in FP64 mode (opts->precision must be 0), with the
+ * gmaf_solve_joint computes in FP64 mode with the synchronized criterion
+ * (opts->precision and opts->criterion must be 0), with the
  * same arguments minus the context and plus the stream, and allocates nothing:
  * its scratch is a fixed array of GMAF_NOALLOC_SCRATCH_BYTES inside the
  * library, which every GPU that loads the library holds until the process

@@ -78,6 +78,8 @@ bool opts_valid(const gmaf_solver_opts *o)
     if (!(o->eps > 0.0) || !std::isfinite(o->eps)) return false;
     if (o->max_iter < 0) return false;
     if (o->precision != 0 && o->precision != 1) return false;
+    if (o->criterion != 0 && o->criterion != 1) return false;
+    if (o->criterion == 1 && o->precision != 0) return false;    // asynchronized: FP64 only
     return true;
 }
 
@@ -136,8 +138,8 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     const char *fv = std::getenv("GMAF_VARIANT");
     c->force_variant = fv ? std::atoi(fv) : -1;
     const char *ie = std::getenv("GMAF_INNER_EPS");
-    c->inner_floor = ie ? std::atof(ie) : 1e-6;
-    if (!(c->inner_floor > 0.0 && c->inner_floor < 0.5)) c->inner_floor = 1e-6;
+    c->inner_floor = ie ? std::atof(ie) : 5e-7;
+    if (!(c->inner_floor > 0.0 && c->inner_floor < 0.5)) c->inner_floor = 5e-7;
     *out = c;
     return GMAF_OK;
 }

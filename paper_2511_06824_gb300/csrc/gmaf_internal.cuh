@@ -90,6 +90,8 @@ enum BufId {
     // mixed-precision workspace
     B_D32, B_INVD32, B_AE32, B_AN32, B_B32, B_X32, B_R032, B_R132, B_U032, B_U132, B_Z32, B_V32,
     B_R64,
+    // asynchronized criterion: per-condition descriptors
+    B_ASYNC,
     B_COUNT
 };
 

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "gmaf_internal.cuh"
 #include "gmaf_pcg_kernels.cuh"
@@ -504,6 +505,206 @@ static int read_scalars(gmaf_ctx *ctx, const Scalars *d_sc, Scalars *h_sc)
     return GMAF_OK;
 }
 
+// ---------------------------------------------------------------- asynchronized criterion
+//
+// Eq. 3.10: condition k is its own PCG (own alpha, beta, d, Table 1) and stops
+// when ||A_k p_k - S_k|| / ||S_k|| <= eps.  All conditions run in one
+// persistent launch per CG phase (k_mphase_a/b over one-condition groups); a
+// condition that has converged drops out through the done flag of its
+// scalars, on the device, with no relaunch or resizing from the host.  The
+// host reads the "every condition done" flag once per kAsyncChunk iterations.
+// After the loop each condition gets the FP64 true-residual check of the
+// synchronized path (one restart from the true residual if it fails).  FP64.
+constexpr int kAsyncChunk = 32;
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <int VEC, int TY, int MINB>
+static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot_host,
+                         const double *D, const double *invD, const double *aE, const double *aN,
+                         const double *S, double *p, const gmaf_solver_opts *opts,
+                         gmaf_solve_info *info)
+{
+    cudaStream_t s = ctx->stream;
+    constexpr int W = 32 * VEC;
+    const long long n = (long long)nth * nz;
+    Scalars *scal = (Scalars *)ctx->buf[B_SCAL];
+    Scalars *msc = scal + 2;                   // tickets and task counters of the batched launches
+    Scalars *gsc = scal + 3;                   // [K] per-condition PCG scalars
+    Scalars *rsc = scal + 3 + kMaxCond;        // [K] per-condition true residuals
+    // device descriptors: MultiDesc, PcgDesc[K], ResidDesc[K], the one-slot table {0}
+    const size_t o_groups = align256(sizeof(MultiDesc<double>));
+    const size_t o_resid = o_groups + align256((size_t)kMaxCond * sizeof(PcgDesc<double>));
+    const size_t o_slot = o_resid + align256((size_t)kMaxCond * sizeof(ResidDesc));
+    GMAF_TRY(ensure(ctx, B_ASYNC, o_slot + 256));
+    char *abase = (char *)ctx->buf[B_ASYNC];
+    MultiDesc<double> *d_m = (MultiDesc<double> *)abase;
+    PcgDesc<double> *d_groups = (PcgDesc<double> *)(abase + o_groups);
+    ResidDesc *d_rd = (ResidDesc *)(abase + o_resid);
+    int *d_slot0 = (int *)(abase + o_slot);
+
+    const int tiles_x = (nth + W - 1) / W, tiles_y = (nz + TY - 1) / TY;
+    const long long ntiles = (long long)tiles_x * tiles_y;
+    const long long total = ntiles * K;
+    const int gs = stream_grid(n, ctx->num_sms);
+    long long np = 2 * total;
+    if (2LL * gs > np) np = 2LL * gs;
+    GMAF_TRY(ensure(ctx, B_PART, (size_t)np * sizeof(double)));
+    double *partials = (double *)ctx->buf[B_PART];
+
+    std::vector<PcgDesc<double>> g(K);
+    std::vector<ResidDesc> rd(K);
+    double *z = (double *)ctx->buf[B_Z], *v = (double *)ctx->buf[B_V];
+    double *u0 = (double *)ctx->buf[B_U0], *u1 = (double *)ctx->buf[B_U1];
+    double *r0 = (double *)ctx->buf[B_R0], *r1 = (double *)ctx->buf[B_R1];
+    for (int k = 0; k < K; ++k) {
+        const long long o = (long long)k * n, c = (long long)cslot_host[k] * n;
+        PcgDesc<double> &h = g[k];
+        h = PcgDesc<double>{};
+        h.nth = nth;
+        h.nz = nz;
+        h.K = 1;
+        h.tiles_x = tiles_x;
+        h.tiles_y = tiles_y;
+        h.precond = opts->precond;
+        h.zero_init = opts->zero_init;
+        h.use_cond = 0;
+        h.n = n;
+        h.ntiles = ntiles;
+        h.sgroups = 1;
+        h.D = D + c;
+        h.invD = invD + c;
+        h.aE = aE + c;
+        h.aN = aN + c;
+        h.cslot = d_slot0;
+        h.b = S + o;
+        h.p = p + o;
+        h.z = z + o;
+        h.v = v + o;
+        h.u[0] = u0 + o;
+        h.u[1] = u1 + o;
+        h.r[0] = r0 + o;
+        h.r[1] = r1 + o;
+        h.omega = opts->omega;
+        h.c1 = opts->omega * (2.0 - opts->omega);
+        h.eps = opts->eps;
+        h.max_iter = opts->max_iter;
+        h.sc = gsc + k;
+        h.partials = partials;
+        ResidDesc &q = rd[k];
+        q = ResidDesc{};
+        q.nth = nth;
+        q.nz = nz;
+        q.K = 1;
+        q.n = n;
+        q.D = D + c;
+        q.aE = aE + c;
+        q.aN = aN + c;
+        q.cslot = d_slot0;
+        q.S = S + o;
+        q.p = p + o;
+        q.sc = rsc + k;
+        q.partials = partials;
+    }
+    MultiDesc<double> hm{};
+    hm.ngroups = K;
+    hm.total_tasks = (unsigned)total;
+    for (int k = 0; k <= K; ++k) hm.task_off[k] = (unsigned)(ntiles * k);
+    hm.groups = d_groups;
+    hm.msc = msc;
+    hm.partials = partials;
+    const int zero = 0;
+    // pageable sources: each copy has consumed its source when it returns
+    GMAF_CUDA(cudaMemcpyAsync(d_slot0, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    GMAF_CUDA(cudaMemcpyAsync(d_groups, g.data(), (size_t)K * sizeof(PcgDesc<double>),
+                              cudaMemcpyHostToDevice, s));
+    GMAF_CUDA(cudaMemcpyAsync(d_m, &hm, sizeof(hm), cudaMemcpyHostToDevice, s));
+
+    const void *kb_init = (const void *)k_phase_b<double, VEC, TY, MINB, true, 0>;
+    const int grid_b = phase_grid(kb_init, ntiles, ctx->num_sms);
+    const int grid_m = phase_grid((const void *)k_mphase_b<double, VEC, TY, MINB>, total, ctx->num_sms);
+    // start: r0 = S_k - A_k p0, z0, d0 and the first criterion test, per condition
+    for (int k = 0; k < K; ++k) {
+        k_reset<<<1, 32, 0, s>>>(gsc + k, 0);
+        k_init_r<double><<<gs, kThreads, 0, s>>>(d_groups + k);
+        GMAF_CUDA(launch<double>(kb_init, grid_b, d_groups + k, s));
+    }
+    GMAF_CUDA(cudaGetLastError());
+    std::vector<Scalars> hg(K), hr(K);
+    std::vector<int> ran(K, 1), restarted(K, 0), final_ok(K, 0);
+    std::vector<double> true_rel(K, 0.0);
+    int *done_h = (int *)ctx->pinned;
+    for (;;) {
+        GMAF_CUDA(cudaMemsetAsync(msc, 0, sizeof(Scalars), s));
+        for (long long it = 0; it <= (long long)opts->max_iter + 2 * kAsyncChunk; it += kAsyncChunk) {
+            for (int q = 0; q < kAsyncChunk; ++q) {
+                k_mphase_a<double, VEC, TY, MINB><<<grid_m, kThreads, 0, s>>>(d_m);
+                k_mphase_b<double, VEC, TY, MINB><<<grid_m, kThreads, 0, s>>>(d_m);
+            }
+            GMAF_CUDA(cudaGetLastError());
+            GMAF_CUDA(cudaMemcpyAsync(done_h, &msc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            GMAF_CUDA(cudaStreamSynchronize(s));
+            if (*done_h) break;
+        }
+        // the deferred p += alpha u of each condition that ran, then its true residual
+        GMAF_CUDA(cudaMemcpyAsync(hg.data(), gsc, (size_t)K * sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+        GMAF_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < K; ++k) {
+            if (!ran[k]) continue;
+            k_finalize<double><<<gs, kThreads, 0, s>>>(d_groups + k);
+            rd[k].r = g[k].r[hg[k].iter & 1];        // where a restart reads it
+            GMAF_CUDA(cudaMemcpyAsync(d_rd + k, &rd[k], sizeof(ResidDesc), cudaMemcpyHostToDevice, s));
+            k_resid64<<<gs, kThreads, 0, s>>>(d_rd + k);
+        }
+        GMAF_CUDA(cudaGetLastError());
+        GMAF_CUDA(cudaMemcpyAsync(hr.data(), rsc, (size_t)K * sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+        GMAF_CUDA(cudaStreamSynchronize(s));
+        bool again = false;
+        for (int k = 0; k < K; ++k) {
+            if (!ran[k]) continue;
+            ran[k] = 0;
+            true_rel[k] = hr[k].true_rel;
+            if (hg[k].zero_rhs) {
+                GMAF_CUDA(cudaMemsetAsync(p + (long long)k * n, 0, (size_t)n * sizeof(double), s));
+                true_rel[k] = 0.0;
+            }
+            if (hg[k].status != 0 || hr[k].status != 0) continue;
+            if ((hg[k].converged || hg[k].zero_rhs) && true_rel[k] <= 10.0 * opts->eps) {
+                final_ok[k] = 1;
+                continue;
+            }
+            if (restarted[k] || hg[k].iter >= opts->max_iter) continue;
+            // restart condition k from its true residual (already in r[iter & 1])
+            restarted[k] = 1;
+            ran[k] = 1;
+            again = true;
+            k_reset<<<1, 32, 0, s>>>(gsc + k, 1);
+            GMAF_CUDA(launch<double>(kb_init, grid_b, d_groups + k, s));
+        }
+        GMAF_CUDA(cudaGetLastError());
+        if (!again) break;
+    }
+    GMAF_CUDA(cudaStreamSynchronize(s));
+    gmaf_solve_info inf{};
+    int status = GMAF_OK;
+    for (int k = 0; k < K; ++k) {
+        inf.iterations = std::max(inf.iterations, hg[k].iter);
+        inf.iterations_sum += hg[k].iter;
+        inf.rel_residual = std::max(inf.rel_residual, hg[k].rel);
+        inf.true_rel_residual = std::max(inf.true_rel_residual, true_rel[k]);
+        inf.restarts += restarted[k];
+        const int st = hg[k].status != 0 ? hg[k].status : hr[k].status;
+        if (st != 0 && status == GMAF_OK) status = st;
+        if (!final_ok[k] && st == 0 && status == GMAF_OK) status = GMAF_NOT_CONVERGED;
+    }
+    inf.status = status;
+    inf.outer_iterations = 1;
+    inf.kernel_variant = 1000 * VEC + 10 * TY + MINB;
+    inf.tasks = (int)total;
+    *info = inf;
+    return status;
+}
+
 int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const int *cslot_host,
                        const double *D, const double *aE, const double *aN, const double *S,
                        double *p, const gmaf_solver_opts *opts, gmaf_solve_info *info)
@@ -513,7 +714,9 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     const long long N = n * K;
     const long long m = n * nslots;
     gmaf_solve_info inf{};
-    GMAF_TRY(ensure(ctx, B_SCAL, 2 * sizeof(Scalars)));
+    // [0] PCG run, [1] outer / true residual, [2] batched-launch tickets, then the
+    // per-condition scalars of the asynchronized criterion ([kMaxCond] PCG, [kMaxCond] residual)
+    GMAF_TRY(ensure(ctx, B_SCAL, (3 + 2 * kMaxCond) * sizeof(Scalars)));
     Scalars *dsc = (Scalars *)ctx->buf[B_SCAL];        // PCG run (FP64, or FP32 inner)
     Scalars *dsc_outer = dsc + 1;                       // FP64 residual of the outer loop
     GMAF_TRY(ensure(ctx, B_CSLOT, kMaxCond * sizeof(int)));
@@ -550,6 +753,12 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         for (int b : bufs) GMAF_TRY(ensure(ctx, b, (size_t)N * sizeof(double)));
         k_invd64<<<stream_grid(m, ctx->num_sms), kThreads, 0, s>>>(D, (double *)ctx->buf[B_INVD], m);
         GMAF_CUDA(cudaGetLastError());
+        if (opts->criterion == 1) {
+            const bool vec = (nth % 2) == 0;     // 16-byte rows of doubles in every condition
+            const double *iv = (const double *)ctx->buf[B_INVD];
+            return vec ? solve_async64<2, 32, 2>(ctx, nth, nz, K, cslot_host, D, iv, aE, aN, S, p, opts, info)
+                       : solve_async64<1, 32, 3>(ctx, nth, nz, K, cslot_host, D, iv, aE, aN, S, p, opts, info);
+        }
         PcgRun<double> run{};
         PcgDesc<double> &h = run.h;
         h.nth = nth;
@@ -604,6 +813,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
                 true_rel = 0.0;
             }
             inf.iterations = hsc->iter;
+            inf.iterations_sum = hsc->iter * K;
             inf.rel_residual = hsc->rel;
             inf.true_rel_residual = true_rel;
             inf.restarts = restarted;
@@ -731,6 +941,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         if (hsc->iter == 0) break;     // no progress possible
     }
     inf.iterations = total_inner;
+    inf.iterations_sum = total_inner * K;
     inf.outer_iterations = outer;
     inf.kernel_variant = run.ks.id;
     inf.tasks = (int)run.h.ntiles;
@@ -804,7 +1015,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     using namespace gmaf;
     if (!grid || !D || !aE || !aN || !S || !p) return GMAF_INVALID_ARG;
     if (grid->n_theta < 3 || grid->n_z < 2 || n_cond < 1 || n_cond > kMaxCond) return GMAF_INVALID_ARG;
-    if (!opts_valid(opts) || opts->precision != 0) return GMAF_INVALID_ARG;
+    if (!opts_valid(opts) || opts->precision != 0 || opts->criterion != 0) return GMAF_INVALID_ARG;
     const int nth = grid->n_theta, nz = grid->n_z, K = n_cond;
     const long long n = (long long)nth * nz;
     const long long N = n * K;

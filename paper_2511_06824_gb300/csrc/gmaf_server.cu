@@ -215,7 +215,7 @@ static void carve(gmaf_server *sv, Request *r)
     r->v32 = (float *)take((size_t)N * 4);
 }
 
-static constexpr double kInnerFloor = 1e-6;
+static constexpr double kInnerFloor = 5e-7;
 static constexpr int kMaxOuter = 12;
 
 // Start (or restart) the inner FP32 solve of a request from its current r64.

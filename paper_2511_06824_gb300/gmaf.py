@@ -57,14 +57,15 @@ class gmaf_state(ctypes.Structure):
 class gmaf_solver_opts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("omega", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("zero_init", ctypes.c_int32)]
+                ("zero_init", ctypes.c_int32), ("criterion", ctypes.c_int32)]
 
 
 class gmaf_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
                 ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
-                ("kernel_variant", ctypes.c_int32), ("tasks", ctypes.c_int32)]
+                ("kernel_variant", ctypes.c_int32), ("tasks", ctypes.c_int32),
+                ("iterations_sum", ctypes.c_int32)]
 
 
 class gmaf_request(ctypes.Structure):
@@ -182,9 +183,9 @@ def state_vector(st: gmaf_state) -> np.ndarray:
 
 
 def solver_opts(precond=1, omega=1.2, eps=1e-10, max_iter=100000, precision=0,
-                zero_init=1) -> gmaf_solver_opts:
+                zero_init=1, criterion=0) -> gmaf_solver_opts:
     return gmaf_solver_opts(int(precond), float(omega), float(eps), int(max_iter), int(precision),
-                            int(zero_init))
+                            int(zero_init), int(criterion))
 
 
 def _dev(t, n: int, name: str) -> int:

@@ -69,9 +69,9 @@ int main(void) {
   P(gmaf_result, state) P(gmaf_result, J) P(gmaf_result, G)
   P(gmaf_texture, radius) P(gmaf_texture, offset_z) P(gmaf_state, edot)
   P(gmaf_solver_opts, omega) P(gmaf_solver_opts, eps) P(gmaf_solver_opts, max_iter)
-  P(gmaf_solver_opts, precision) P(gmaf_solver_opts, zero_init)
+  P(gmaf_solver_opts, precision) P(gmaf_solver_opts, zero_init) P(gmaf_solver_opts, criterion)
   P(gmaf_solve_info, rel_residual) P(gmaf_solve_info, true_rel_residual)
-  P(gmaf_solve_info, kernel_variant) P(gmaf_solve_info, tasks)
+  P(gmaf_solve_info, kernel_variant) P(gmaf_solve_info, tasks) P(gmaf_solve_info, iterations_sum)
   P(gmaf_physics, p_case)
   return 0;
 }

@@ -276,6 +276,56 @@ def test_static_schedule_is_deterministic_and_graph_matches_host_loop(g, monkeyp
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
+# asynchronized criterion (Eq. 3.10): each condition is its own PCG, so the oracle is
+# the oracle's solve of each condition alone
+@pytest.mark.parametrize("nth,nz,K,precond", [(130, 45, 9, 1), (131, 7, 3, 1), (96, 40, 4, 0),
+                                              (3, 2, 2, 1)])
+def test_asynchronized_criterion_matches_per_condition_oracle(g, ctx, nth, nz, K, precond):
+    conds = states(K, seed=nth + 3 * K)
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
+    n = K * nth * nz
+    p = zeros(n)
+    opts = g.solver_opts(precond=precond, eps=1e-10, criterion=1)
+    st, it, rel = g.gmaf_solve_joint(ctx, nth, nz, K, dev(D), dev(aE), dev(aN), dev(S), p, opts)
+    info = g.gmaf_last_solve_info(ctx)
+    assert st == 0 and rel <= 1e-9
+    pg = host(p).reshape(K, nz, nth)
+    its = []
+    for k in range(K):
+        sl = slice(k, k + 1)
+        sto, po, ito, _, _ = oracle.solve_joint(nth, nz, D[sl], aE[sl], aN[sl], S[sl],
+                                                precond=precond, omega=1.2, eps=1e-10)
+        assert sto == 0
+        its.append(ito)
+        assert rel_l2(pg[k], po) <= 1e-9, k
+    assert abs(info["iterations"] - max(its)) <= 2, (info["iterations"], its)
+    assert abs(info["iterations_sum"] - sum(its)) <= 2 * K, (info["iterations_sum"], its)
+
+
+def test_asynchronized_picard_step_and_option_checks(g, ctx):
+    rng = np.random.default_rng(21)
+    st0 = inputs.random_state(rng)
+    tex = tex_dimples()
+    dt = 2.7777777777777778e-4
+    F = np.array([30.0, -15.0, 6.0, -3.0])
+    res = {}
+    for crit in (0, 1):
+        res[crit] = g.gmaf_picard_step(ctx, 96, 48, PHYS, tex, st0, st0[:4], dt, F, 2e-8, 1e-6,
+                                       g.solver_opts(eps=1e-12, criterion=crit))
+        info = g.gmaf_last_solve_info(ctx)
+        if crit == 1:
+            assert info["iterations_sum"] > info["iterations"]
+        else:
+            assert info["iterations_sum"] == 9 * info["iterations"]
+    assert load_err(res[1]["loads"], res[0]["loads"]) <= 1e-7
+    p = zeros(2 * 64 * 32)
+    so, D, aE, aN, S = oracle.assemble_joint(64, 32, PHYS, inputs.smooth_texture(), states(2))
+    for bad in (g.solver_opts(criterion=1, precision=1), g.solver_opts(criterion=2)):
+        with pytest.raises(g.GmafError) as ei:
+            g.gmaf_solve_joint(ctx, 64, 32, 2, dev(D), dev(aE), dev(aN), dev(S), p, bad)
+        assert ei.value.status == g.GMAF_INVALID_ARG
+
+
 def test_hbm_budget_is_enforced(g):
     c = g.Context(hbm_budget_bytes=1 << 20)
     n = 9 * 256 * 128

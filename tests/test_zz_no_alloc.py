@@ -73,6 +73,6 @@ def test_noalloc_refuses_problems_beyond_its_scratch(g):
     st, it, rel = g.gmaf_solve_joint_noalloc(n_theta, n_z, K, big, big, big, big, big,
                                              allow=(g.GMAF_OUT_OF_MEMORY,))
     assert st == g.GMAF_OUT_OF_MEMORY
-    with pytest.raises(g.GmafError):
-        g.gmaf_solve_joint_noalloc(64, 32, 1, small, small, small, small, small,
-                                   g.solver_opts(precision=1))
+    for bad in (g.solver_opts(precision=1), g.solver_opts(criterion=1)):
+        with pytest.raises(g.GmafError):
+            g.gmaf_solve_joint_noalloc(64, 32, 1, small, small, small, small, small, bad)
