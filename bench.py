@@ -149,8 +149,10 @@ class ClockSampler:
 
 
 def source_hash() -> str:
+    """Hash of the device code of the PCG phase kernels (the launch shape is keyed
+    separately, by the kernel variant)."""
     h = hashlib.sha256()
-    for f in ("gmaf_pcg.cu", "gmaf_pcg_kernels.cuh", "gmaf_internal.cuh"):
+    for f in ("gmaf_pcg_kernels.cuh",):
         with open(os.path.join(ROOT, "paper_2511_06824_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
