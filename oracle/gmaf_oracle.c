@@ -370,7 +370,11 @@ static void joint_apply(const joint *J, int part, const double *x, double *y)
  *  precond 1: ASSOR-II (Eq. 3.3-3.6), in the paper's two steps:
  *     v = (I - w D^-1 L) D^-1 r                      (Eq. 3.5)
  *     z = (2 - w) w (I - w D^-1 L^T) v               (Eq. 3.6)
- *  L^T is applied as the strictly upper triangle of A (A is symmetric). */
+ *  L^T is applied as the strictly upper triangle of A (A is symmetric).
+ *  precond 2: ASSOR-I (Eq. 3.2), a diagonal preconditioner:
+ *     {M^-1}_ii = w (2 - w) / {(D + w L) D^-1 (D + w L)^T}_ii,
+ *  where, B = D + w L being lower triangular with diagonal D,
+ *     {B D^-1 B^T}_ii = sum_k B_ik^2 / D_k = D_i + w^2 sum_{k < i} L_ik^2 / D_k. */
 static void joint_precond(const joint *J, int precond, double omega,
                           const double *r, double *z, double *t1, double *t2)
 {
@@ -378,6 +382,23 @@ static void joint_precond(const joint *J, int precond, double omega,
     const double *D = J->D;
     if (precond == 0) {
         for (size_t k = 0; k < N; ++k) z[k] = r[k] / D[k];
+        return;
+    }
+    if (precond == 2) {
+        for (int c = 0; c < J->ncond; ++c) {
+            const csr *m = &J->blk[c];
+            size_t o = (size_t)c * J->n;
+            for (size_t row = 0; row < m->n; ++row) {
+                double s = 0.0;
+                for (size_t k = m->rowptr[row]; k < m->rowptr[row + 1]; ++k) {
+                    size_t col = m->col[k];
+                    if (col >= row) continue;               /* strictly lower */
+                    s += m->val[k] * m->val[k] / D[o + col];
+                }
+                double diag = D[o + row] + omega * omega * s;
+                z[o + row] = omega * (2.0 - omega) * r[o + row] / diag;
+            }
+        }
         return;
     }
     /* t1 = D^-1 r */
@@ -448,8 +469,8 @@ int oracle_solve_joint(int nth, int nz, int ncond, const double *D,
                        double *out)
 {
     if (nth < 3 || nz < 2 || ncond < 1 || !(eps > 0.0) || max_iter < 0 ||
-        (precond == 1 && !(omega > 0.0 && omega < 2.0)) ||
-        (precond != 0 && precond != 1))
+        (precond != 0 && !(omega > 0.0 && omega < 2.0)) ||
+        (precond != 0 && precond != 1 && precond != 2))
         return OR_INVALID;
     joint J;
     int st = joint_build(nth, nz, ncond, D, aE, aN, &J);

@@ -188,7 +188,7 @@ def test_parallel_eccentric_pressure_is_linear_in_z():
     np.testing.assert_allclose(p, np.repeat(exact[:, None], nth, axis=1), rtol=1e-9)
 
 
-@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("precond", [0, 1, 2])
 def test_pcg_matches_dense_direct_solve(precond):
     nth, nz = 16, 8
     st = state((5e-6, 3e-6, 8e-6, -2e-6), (6e-5, -4e-5, 2e-5, 9e-5))
@@ -247,6 +247,33 @@ def test_assor_apply_matches_dense_definition_and_is_spd(omega):
     assert np.linalg.eigvalsh(0.5 * (cols + cols.T)).min() > 0
     zj = oracle.apply_precond(nth, nz, D, aE, aN, r, precond=0)
     np.testing.assert_array_equal(zj, r / D.ravel())
+
+
+@pytest.mark.parametrize("omega", [0.6, 1.2, 1.8])
+def test_assor1_is_the_diagonal_of_the_dense_ssor_product(omega):
+    """Eq. 3.2: {M^-1}_ii = w (2 - w) / {(D + w L) D^-1 (D + w L)^T}_ii, written with
+    dense numpy factors (L = strict lower triangle in the joint index order, so the
+    periodic couplings of column n_theta - 1 to column 0 are lower, those of column 0
+    to column n_theta - 1 upper)."""
+    nth, nz = 7, 5
+    rng = np.random.default_rng(17)
+    states = [inputs.random_state(rng) for _ in range(2)]
+    s, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_default(), states)
+    n = nth * nz
+    r = rng.standard_normal(2 * n)
+    want = np.empty(2 * n)
+    for k in range(2):
+        A = oracle.dense_matrix(nth, nz, D[k], aE[k], aN[k])
+        Dm = np.diag(np.diag(A))
+        B = Dm + omega * np.tril(A, -1)
+        diag = np.diag(B @ np.linalg.inv(Dm) @ B.T)
+        want[k * n:(k + 1) * n] = omega * (2 - omega) * r[k * n:(k + 1) * n] / diag
+    z = oracle.apply_precond(nth, nz, D, aE, aN, r, precond=2, omega=omega)
+    np.testing.assert_allclose(z, want, rtol=1e-13, atol=0)
+    # a wrong lower set (e.g. the west neighbour of column 0 counted as lower) would
+    # change row 0 of each block: check that the first rows see only their south
+    # neighbour and the last column its west and wrapped east neighbours
+    assert not np.allclose(want, omega * (2 - omega) * r / D.ravel())
 
 
 def test_assor_needs_fewer_iterations_than_jacobi_and_agrees():
