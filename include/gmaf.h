@@ -78,7 +78,8 @@ typedef struct {
 /* Eccentricities e1, e2 at z = 0 and e3, e4 at z = L [m] and their rates [m/s] (Eq. 2.3). */
 typedef struct { double e[4], edot[4]; } gmaf_state;
 
-/* precond: 0 Jacobi (Eq. 2.8), 1 ASSOR-II (Eq. 3.4).  omega in (0, 2).
+/* precond: 0 Jacobi (Eq. 2.8), 1 ASSOR-II (Eq. 3.4), 2 ASSOR-I (Eq. 3.2, the
+ *   diagonal w (2 - w) / {(D + w L) D^-1 (D + w L)^T}_ii).  omega in (0, 2).
  * eps: tolerance of the convergence criterion below.
  * max_iter: PCG iteration budget (inner iterations in mixed precision).
  * precision: 0 FP64 throughout; 1 mixed - FP32 stencil, preconditioner and

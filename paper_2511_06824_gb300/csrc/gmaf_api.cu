@@ -73,8 +73,8 @@ bool geom_valid(const gmaf_grid *g, const gmaf_physics *ph, const gmaf_texture *
 bool opts_valid(const gmaf_solver_opts *o)
 {
     if (!o) return false;
-    if (o->precond != 0 && o->precond != 1) return false;
-    if (o->precond == 1 && !(o->omega > 0.0 && o->omega < 2.0)) return false;
+    if (o->precond != 0 && o->precond != 1 && o->precond != 2) return false;
+    if (o->precond != 0 && !(o->omega > 0.0 && o->omega < 2.0)) return false;
     if (!(o->eps > 0.0) || !std::isfinite(o->eps)) return false;
     if (o->max_iter < 0) return false;
     if (o->precision != 0 && o->precision != 1) return false;

@@ -505,6 +505,60 @@ static int read_scalars(gmaf_ctx *ctx, const Scalars *d_sc, Scalars *h_sc)
     return GMAF_OK;
 }
 
+// ---------------------------------------------------------------- ASSOR-I
+//
+// Eq. 3.2: {M^-1}_ii = w (2 - w) / {(D + w L) D^-1 (D + w L)^T}_ii
+//                    = w (2 - w) / (D_i + w^2 sum_{k in low(i)} a_ik^2 / D_k),
+// low(i) = {S; W if i > 0; E across the wrap if i = n_theta - 1}, the strictly
+// lower couplings in the joint index order.  The PCG phases apply it as a
+// diagonal, through the Jacobi path.  With outer given the result is for the
+// FP32 matrix scale * A (outer->scale, set by k_to_f32), i.e. divided by scale.
+template <typename T>
+static __global__ void __launch_bounds__(kThreads)
+k_assor1_diag(const double *__restrict__ D, const double *__restrict__ aE,
+              const double *__restrict__ aN, int nth, int nz, long long m, double omega,
+              const Scalars *__restrict__ outer, T *__restrict__ out)
+{
+    const long long n = (long long)nth * nz;
+    const double scale = outer ? outer->scale : 1.0;
+    const double c1 = omega * (2.0 - omega), w2 = omega * omega;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long P = q % n;
+        const int j = (int)(P / nth), i = (int)(P - (long long)j * nth);
+        double s = 0.0;
+        if (j > 0) {
+            const double a = aN[q - nth];
+            s += a * a / D[q - nth];
+        }
+        if (i > 0) {
+            const double a = aE[q - 1];
+            s += a * a / D[q - 1];
+        }
+        if (i == nth - 1) {
+            const double a = aE[q];
+            s += a * a / D[q - (nth - 1)];
+        }
+        out[q] = (T)(c1 / (D[q] + w2 * s) / scale);
+    }
+}
+
+// The diagonal the PCG phases divide by: 1/D (Jacobi, ASSOR-II) or ASSOR-I's.
+static void diag_inverse64(const gmaf_solver_opts *opts, const double *D, const double *aE,
+                           const double *aN, int nth, int nz, long long m, double *out, int num_sms,
+                           cudaStream_t s)
+{
+    if (opts->precond == 2)
+        k_assor1_diag<double><<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, aE, aN, nth, nz, m,
+                                                                          opts->omega, nullptr, out);
+    else
+        k_invd64<<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, out, m);
+}
+
+// PCG-kernel preconditioner: ASSOR-II runs its two passes, Jacobi and ASSOR-I
+// divide by the stored diagonal.
+static int kernel_precond(const gmaf_solver_opts *opts) { return opts->precond == 1 ? 1 : 0; }
+
 // ---------------------------------------------------------------- asynchronized criterion
 //
 // Eq. 3.10: condition k is its own PCG (own alpha, beta, d, Table 1) and stops
@@ -566,7 +620,7 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
         h.K = 1;
         h.tiles_x = tiles_x;
         h.tiles_y = tiles_y;
-        h.precond = opts->precond;
+        h.precond = kernel_precond(opts);
         h.zero_init = opts->zero_init;
         h.use_cond = 0;
         h.n = n;
@@ -751,7 +805,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         GMAF_TRY(ensure(ctx, B_INVD, (size_t)m * sizeof(double)));
         const int bufs[] = {B_R0, B_R1, B_U0, B_U1, B_Z, B_V};
         for (int b : bufs) GMAF_TRY(ensure(ctx, b, (size_t)N * sizeof(double)));
-        k_invd64<<<stream_grid(m, ctx->num_sms), kThreads, 0, s>>>(D, (double *)ctx->buf[B_INVD], m);
+        diag_inverse64(opts, D, aE, aN, nth, nz, m, (double *)ctx->buf[B_INVD], ctx->num_sms, s);
         GMAF_CUDA(cudaGetLastError());
         if (opts->criterion == 1) {
             const bool vec = (nth % 2) == 0;     // 16-byte rows of doubles in every condition
@@ -765,7 +819,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         h.nz = nz;
         h.K = K;
         h.n = n;
-        h.precond = opts->precond;
+        h.precond = kernel_precond(opts);
         h.zero_init = opts->zero_init;
         h.D = D;
         h.invD = (const double *)ctx->buf[B_INVD];
@@ -851,6 +905,9 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     k_to_f32<<<stream_grid(m, ctx->num_sms), kThreads, 0, s>>>(
         D, aE, aN, (float *)ctx->buf[B_D32], (float *)ctx->buf[B_INVD32], (float *)ctx->buf[B_AE32],
         (float *)ctx->buf[B_AN32], m, dsc_outer);
+    if (opts->precond == 2)
+        k_assor1_diag<float><<<stream_grid(m, ctx->num_sms), kThreads, 0, s>>>(
+            D, aE, aN, nth, nz, m, opts->omega, dsc_outer, (float *)ctx->buf[B_INVD32]);
     GMAF_CUDA(cudaGetLastError());
     if (opts->zero_init) GMAF_CUDA(cudaMemsetAsync(p, 0, (size_t)N * sizeof(double), s));
 
@@ -860,7 +917,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     h.nz = nz;
     h.K = K;
     h.n = n;
-    h.precond = opts->precond;
+    h.precond = kernel_precond(opts);
     h.zero_init = 1;
     h.D = (const float *)ctx->buf[B_D32];
     h.invD = (const float *)ctx->buf[B_INVD32];
@@ -1036,7 +1093,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     h.nz = nz;
     h.K = K;
     h.n = n;
-    h.precond = opts->precond;
+    h.precond = kernel_precond(opts);
     h.zero_init = opts->zero_init;
     h.use_cond = 0;
     double *vbase = (double *)(base + kNaVec);
@@ -1102,7 +1159,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    k_invd64<<<stream_grid(N, num_sms), kThreads, 0, s>>>(D, invD, N);
+    diag_inverse64(opts, D, aE, aN, nth, nz, N, invD, num_sms, s);
 
     Scalars hs{}, hr{};
     int restarted = 0;

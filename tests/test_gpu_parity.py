@@ -141,6 +141,8 @@ def solve_both(g, ctx, nth, nz, tex, conds, precond=1, omega=1.2, eps=1e-10, pre
     (96, 40, 4, False, 0),        # Jacobi
     (3, 2, 1, False, 1),          # smallest grid
     (257, 9, 2, True, 1),         # one tile row, ragged in theta
+    (130, 45, 9, True, 2),        # ASSOR-I (Eq. 3.2)
+    (3, 2, 2, False, 2),          # ASSOR-I, smallest grid (every column touches the wrap)
 ])
 def test_fp64_solve_matches_oracle(g, ctx, nth, nz, K, textured, precond):
     tex = tex_dimples() if textured else inputs.smooth_texture()
@@ -160,10 +162,11 @@ def test_fp64_iterates_track_the_oracle_tightly(g, ctx):
     assert rel_l2(p, po) <= 1e-11
 
 
-@pytest.mark.parametrize("nth,nz,K", [(64, 32, 1), (130, 45, 9)])
-def test_mixed_precision_solve_matches_fp64_oracle(g, ctx, nth, nz, K):
+@pytest.mark.parametrize("nth,nz,K,precond", [(64, 32, 1, 1), (130, 45, 9, 1), (132, 40, 9, 2)])
+def test_mixed_precision_solve_matches_fp64_oracle(g, ctx, nth, nz, K, precond):
     conds = states(K, seed=7)
-    p, it, rel, po, ito, arrs = solve_both(g, ctx, nth, nz, tex_dimples(), conds, precision=1)
+    p, it, rel, po, ito, arrs = solve_both(g, ctx, nth, nz, tex_dimples(), conds, precision=1,
+                                           precond=precond)
     assert rel <= 1e-10
     assert rel_l2(p, po) <= 1e-6
     info = g.gmaf_last_solve_info(ctx)
@@ -279,7 +282,7 @@ def test_static_schedule_is_deterministic_and_graph_matches_host_loop(g, monkeyp
 # asynchronized criterion (Eq. 3.10): each condition is its own PCG, so the oracle is
 # the oracle's solve of each condition alone
 @pytest.mark.parametrize("nth,nz,K,precond", [(130, 45, 9, 1), (131, 7, 3, 1), (96, 40, 4, 0),
-                                              (3, 2, 2, 1)])
+                                              (3, 2, 2, 1), (100, 30, 3, 2)])
 def test_asynchronized_criterion_matches_per_condition_oracle(g, ctx, nth, nz, K, precond):
     conds = states(K, seed=nth + 3 * K)
     so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
