@@ -84,6 +84,12 @@ def lib():
                                               ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int, _D, _D, _D, _I,
                                               _D, _D])
+            L.oracle_picard_step_simplified.restype = ctypes.c_int
+            L.oracle_picard_step_simplified.argtypes = ([ctypes.c_int, ctypes.c_int, _D, _D, _D,
+                                                         ctypes.c_double, _D, ctypes.c_double,
+                                                         ctypes.c_int, ctypes.c_double,
+                                                         ctypes.c_double, ctypes.c_int, _D, _D, _D,
+                                                         _I])
             _lib = L
     return _lib
 
@@ -197,6 +203,25 @@ def generalized_force(L, F6):
     G = np.zeros(4)
     lib().oracle_generalized_force(float(L), _p(F6), _p(G))
     return G
+
+
+def picard_step_simplified(nth, nz, phys, tex, state, dt, F_ext, d_edot, precond=1, omega=1.2,
+                           eps=1e-10, max_iter=100000):
+    """One conventional (simplified) Picard iteration, Eq. 2.20-2.22, on the 5-condition
+    joint batch (base + 4 rate perturbations).
+
+    Returns dict(status, state, loads[12], J[6,8] (e-columns zero), G[4], iters).
+    """
+    phys, tex = _f64(phys), _f64(tex)
+    st_vec = _f64(state).copy()
+    F_ext = _f64(F_ext)
+    loads_out, J, G = np.zeros(12), np.zeros(48), np.zeros(4)
+    it = ctypes.c_int(0)
+    st = lib().oracle_picard_step_simplified(nth, nz, _p(phys), _p(tex), _p(st_vec), float(dt),
+                                             _p(F_ext), float(d_edot), int(precond), float(omega),
+                                             float(eps), int(max_iter), _p(loads_out), _p(J),
+                                             _p(G), ctypes.byref(it))
+    return dict(status=st, state=st_vec, loads=loads_out, J=J.reshape(6, 8), G=G, iters=it.value)
 
 
 def picard_step(nth, nz, phys, tex, state, e_prev, dt, F_ext, d_e, d_edot,

@@ -766,3 +766,89 @@ done:
     free(D); free(aE); free(aN); free(S); free(p);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* One conventional (simplified) Picard iteration, Eq. 2.20-2.22: the       */
+/* Jacobian F_,e is dropped, so only the base condition and the 4 rate      */
+/* perturbations are solved (5 conditions, one joint system, Eq. 3.9).      */
+/*   F_,edot by forward differences (Eq. 2.14) on the generalized force,    */
+/*   edot_new = edot - [F_,edot]^-1 F            (Eq. 2.21)                 */
+/*   e_new    = e - [F_,edot / dt]^-1 F = e + dt (edot_new - edot)  (2.22)  */
+/* F is the generalized force G of the oil loads plus F_ext.  J_out is the  */
+/* 6 x 8 load Jacobian with its 4 e-columns zero (not computed).            */
+/* ------------------------------------------------------------------------ */
+int oracle_picard_step_simplified(int nth, int nz, const double *phys, const double *tex,
+                                  double *state, double dt, const double *F_ext,
+                                  double d_edot, int precond, double omega, double eps,
+                                  int max_iter, double *loads_out, double *J_out,
+                                  double *G_out, int *iters_out)
+{
+    if (nth < 3 || nz < 2 || !phys || !state || !F_ext || !(d_edot != 0.0))
+        return OR_INVALID;
+    const int K = 5;
+    size_t n = (size_t)nth * (size_t)nz;
+    size_t N = n * (size_t)K;
+    double *D = (double *)malloc(N * sizeof(double));
+    double *aE = (double *)malloc(N * sizeof(double));
+    double *aN = (double *)malloc(N * sizeof(double));
+    double *S = (double *)malloc(N * sizeof(double));
+    double *p = (double *)calloc(N, sizeof(double));
+    int st = OR_OK;
+    if (!D || !aE || !aN || !S || !p) { st = OR_NOMEM; goto done; }
+
+    double cond[5][8];
+    for (int k = 0; k < K; ++k) memcpy(cond[k], state, 8 * sizeof(double));
+    for (int j = 0; j < 4; ++j) cond[1 + j][4 + j] += d_edot;
+    for (int k = 0; k < K; ++k) {
+        size_t o = (size_t)k * n;
+        int s = oracle_assemble(nth, nz, phys, tex, cond[k], D + o, aE + o, aN + o, S + o);
+        if (s) { st = s; goto done; }
+    }
+    int iters = 0;
+    double res[2];
+    int sst = oracle_solve_joint(nth, nz, K, D, aE, aN, S, p, precond, omega, eps,
+                                 max_iter, 1, &iters, res);
+    if (iters_out) *iters_out = iters;
+    if (sst != OR_OK && sst != OR_NOT_CONVERGED) { st = sst; goto done; }
+
+    double Lk[5][12];
+    for (int k = 0; k < K; ++k) {
+        int s = oracle_loads(nth, nz, phys, tex, cond[k], p + (size_t)k * n, Lk[k]);
+        if (s) { st = s; goto done; }
+    }
+    double F[5][6];
+    for (int k = 0; k < K; ++k)
+        for (int c = 0; c < 6; ++c) F[k][c] = Lk[k][c] + Lk[k][6 + c];
+    double J[6][4];
+    for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 4; ++c) J[r][c] = (F[1 + c][r] - F[0][r]) / d_edot;
+    double L = phys[1];
+    double G[4];
+    oracle_generalized_force(L, F[0], G);
+    for (int k = 0; k < 4; ++k) G[k] += F_ext[k];
+    if (loads_out) memcpy(loads_out, Lk[0], 12 * sizeof(double));
+    if (J_out)
+        for (int r = 0; r < 6; ++r)
+            for (int c = 0; c < 8; ++c) J_out[r * 8 + c] = c < 4 ? 0.0 : J[r][c - 4];
+    if (G_out) memcpy(G_out, G, 4 * sizeof(double));
+    if (sst == OR_NOT_CONVERGED) { st = sst; goto done; }
+
+    double Jd[4][4], rhs[4], delta[4];
+    for (int c = 0; c < 4; ++c) {
+        double col[6], g[4];
+        for (int r = 0; r < 6; ++r) col[r] = J[r][c];
+        oracle_generalized_force(L, col, g);
+        for (int r = 0; r < 4; ++r) Jd[r][c] = g[r];
+    }
+    for (int r = 0; r < 4; ++r) rhs[r] = -G[r];
+    int s4 = solve4(Jd, rhs, delta);
+    if (s4) { st = s4; goto done; }
+    for (int k = 0; k < 4; ++k) {
+        state[4 + k] = state[4 + k] + delta[k];     /* Eq. 2.21 */
+        state[k] = state[k] + dt * delta[k];        /* Eq. 2.22 */
+    }
+done:
+    free(D); free(aE); free(aN); free(S); free(p);
+    return st;
+}
+

@@ -521,3 +521,54 @@ def test_picard_iteration_converges_to_force_balance():
         norms.append(np.linalg.norm(r["G"]))
         st = r["state"]
     assert norms[-1] < 1e-6 * norms[0]
+
+
+def test_simplified_picard_jacobian_matches_general_scheme_columns():
+    """Eq. 2.20-2.22 solve only the base and the 4 rate perturbations: their load
+    Jacobian columns equal the rate columns of the general (9-condition) step, and the
+    e-columns are not formed."""
+    nth, nz = 32, 16
+    st = state((6e-6, -3e-6, 2e-6, 5e-6), (3e-5, 1e-5, -2e-5, 4e-5))
+    dt = 2.78e-4
+    Fext = np.array([30.0, -20.0, 5.0, 8.0])
+    rg = oracle.picard_step(nth, nz, PHYS, SMOOTH, st, st[:4] - 1e-7, dt, Fext, 2e-8, 1e-6,
+                            eps=1e-13)
+    rs = oracle.picard_step_simplified(nth, nz, PHYS, SMOOTH, st, dt, Fext, 1e-6, eps=1e-13)
+    assert rs["status"] == oracle.OK and rg["status"] == oracle.OK
+    colscale = np.abs(rg["J"][:, 4:]).max(axis=0, keepdims=True)
+    assert np.max(np.abs(rs["J"][:, 4:] - rg["J"][:, 4:]) / colscale) <= 1e-9
+    assert not np.any(rs["J"][:, :4])
+    np.testing.assert_allclose(rs["loads"], rg["loads"], rtol=1e-10, atol=1e-10)
+
+
+def test_simplified_picard_update_follows_eqs_2_21_2_22():
+    """edot_new = edot - Jd^-1 G (Eq. 2.21) and e_new = e + dt (edot_new - edot)
+    (Eq. 2.22), rebuilt with numpy from the returned Jacobian and generalized force."""
+    nth, nz = 32, 16
+    st = state((6e-6, -3e-6, 2e-6, 5e-6), (3e-5, 1e-5, -2e-5, 4e-5))
+    dt = 2.78e-4
+    Fext = np.array([30.0, -20.0, 5.0, 8.0])
+    r = oracle.picard_step_simplified(nth, nz, PHYS, SMOOTH, st, dt, Fext, 1e-6, eps=1e-13)
+    T = np.array([[1, 0, 0, 0, -1 / L, 0], [0, 1, 0, 1 / L, 0, 0], [0, 0, 0, 0, 1 / L, 0],
+                  [0, 0, 0, -1 / L, 0, 0]])
+    Jd = T @ r["J"][:, 4:]
+    G = T @ _total(r["loads"]) + Fext
+    np.testing.assert_allclose(r["G"], G, rtol=1e-12, atol=1e-9)
+    delta = np.linalg.solve(Jd, -G)
+    np.testing.assert_allclose(r["state"][4:], st[4:] + delta, rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(r["state"][:4], st[:4] + dt * delta, rtol=1e-9, atol=1e-18)
+
+
+def test_simplified_picard_iteration_reaches_force_balance():
+    """At a fixed point of Eq. 2.21 the update is zero, so the generalized force is."""
+    nth, nz = 32, 16
+    st = state((2e-6, 1e-6, 2e-6, 1e-6))
+    dt = 2.78e-4
+    Fext = np.array([40.0, -25.0, 10.0, -5.0])
+    norms = []
+    for _ in range(6):
+        r = oracle.picard_step_simplified(nth, nz, PHYS, SMOOTH, st, dt, Fext, 1e-6, eps=1e-13)
+        assert r["status"] == oracle.OK
+        norms.append(np.linalg.norm(r["G"]))
+        st = r["state"]
+    assert norms[-1] < 1e-9 * norms[0]
