@@ -195,6 +195,21 @@ int gmaf_picard_step(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *p
                      const gmaf_solver_opts *opts, double loads_out[12], double J_out[48],
                      double G_out[4], int32_t *iters_out);
 
+/* One conventional (simplified) Picard iteration, Eq. 2.20-2.22, for comparison
+ * with the general scheme: the Jacobian F_,e is dropped, so only the base
+ * condition and the 4 rate perturbations edot_j + d_edot are assembled and
+ * solved (one joint system of 5 conditions sharing one coefficient set), then
+ *   edot_new = edot - [F_,edot]^-1 G                    (Eq. 2.21)
+ *   e_new    = e + dt (edot_new - edot)                  (Eq. 2.22)
+ * with G the generalized force of the base loads plus F_ext.  Arguments,
+ * outputs and errors as gmaf_picard_step (no e_prev, no d_e); J_out's e-columns
+ * are 0 (not formed).  Synchronises the stream. */
+int gmaf_picard_step_simplified(gmaf_ctx *ctx, const gmaf_grid *grid, const gmaf_physics *phys,
+                                const gmaf_texture *tex, gmaf_state *state, double dt,
+                                const double F_ext[4], double d_edot,
+                                const gmaf_solver_opts *opts, double loads_out[12],
+                                double J_out[48], double G_out[4], int32_t *iters_out);
+
 /* Per-phase kernel timing (tracing).  When enabled (on != 0), the PCG loop of
  * later solves is driven in host chunks instead of the graph WHILE node, with a
  * CUDA event pair around every phase launch on the context's stream; results
@@ -288,10 +303,11 @@ int gmaf_server_poll(gmaf_server *server, gmaf_result *out, int32_t max_results,
 /* Free bytes left in the server's arena. */
 int gmaf_server_free_bytes(const gmaf_server *server, size_t *bytes_out);
 
-/* Copy the 9 pressure fields of the last gmaf_picard_step on this context
- * (condition-major, 9 * n_z * n_theta doubles, device memory p_out) for a
- * step of the given grid; GMAF_INVALID_ARG if the last step had another grid.
- * Asynchronous. */
+/* Copy the pressure fields of the last Picard step on this context
+ * (condition-major, device memory p_out of 9 * n_z * n_theta doubles): the 9
+ * conditions of gmaf_picard_step, or the 5 of gmaf_picard_step_simplified (base,
+ * then edot_1..4 + d_edot; the rest of p_out is left alone), for a step of the
+ * given grid; GMAF_INVALID_ARG if the last step had another grid.  Asynchronous. */
 int gmaf_last_fields(gmaf_ctx *ctx, const gmaf_grid *grid, double *p_out);
 
 /* Static description of a status code. */

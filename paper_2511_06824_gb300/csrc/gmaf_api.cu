@@ -199,7 +199,7 @@ int gmaf_last_fields(gmaf_ctx *c, const gmaf_grid *grid, double *p_out)
 {
     if (!c || !grid || !p_out || !c->buf[B_PP]) return GMAF_INVALID_ARG;
     if (grid->n_theta != c->pp_nth || grid->n_z != c->pp_nz) return GMAF_INVALID_ARG;
-    const size_t bytes = (size_t)9 * grid->n_theta * grid->n_z * sizeof(double);
+    const size_t bytes = (size_t)c->pp_K * grid->n_theta * grid->n_z * sizeof(double);
     return cuda_status(cudaMemcpyAsync(p_out, c->buf[B_PP], bytes, cudaMemcpyDeviceToDevice, c->stream));
 }
 
@@ -300,10 +300,16 @@ int gmaf_integrate_loads(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics 
                         part, tickets, loads, (int *)c->buf[B_FLAGS], c->num_sms, s);
 }
 
-int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phys,
-                     const gmaf_texture *tex, gmaf_state *state, const double e_prev[4], double dt,
-                     const double F_ext[4], double d_e, double d_edot, const gmaf_solver_opts *opts,
-                     double loads_out[12], double J_out[48], double G_out[4], int32_t *iters_out)
+}  // extern "C"
+
+// One Picard iteration on the device: the general double-Jacobian scheme (9
+// conditions in 5 coefficient slots) or, with simplified, the conventional one
+// of Eq. 2.20-2.22 (5 conditions in 1 slot, e_prev unused).
+static int picard_impl(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phys,
+                       const gmaf_texture *tex, gmaf_state *state, const double e_prev[4], double dt,
+                       const double F_ext[4], double d_e, double d_edot,
+                       const gmaf_solver_opts *opts, double loads_out[12], double J_out[48],
+                       double G_out[4], int32_t *iters_out, bool simplified)
 {
     if (!c || !state || !e_prev || !F_ext) return GMAF_INVALID_ARG;
     if (!geom_valid(grid, phys, tex) || !opts_valid(opts)) return GMAF_INVALID_ARG;
@@ -312,7 +318,7 @@ int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phy
         return GMAF_INVALID_ARG;
     for (int q = 0; q < 4; ++q)
         if (!std::isfinite(e_prev[q]) || !std::isfinite(F_ext[q])) return GMAF_INVALID_ARG;
-    const int K = 9, NSLOT = 5;
+    const int K = simplified ? 5 : 9, NSLOT = simplified ? 1 : 5;
     const Geom g = make_geom(grid, phys, tex);
     const size_t n = (size_t)g.nth * g.nz;
     cudaStream_t s = c->stream;
@@ -340,20 +346,24 @@ int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phy
     cudaError_t e = cudaMemsetAsync(c->buf[B_FLAGS], 0, 64, s);
     if (e != cudaSuccess) return cuda_status(e);
     // (a1) fan-out, (a2) assembly of 5 coefficient sets and 9 sources
-    if ((st = launch_fanout(base, d_e, d_edot, conds, cslot_write, s))) return st;
+    if ((st = launch_fanout(base, d_e, d_edot, conds, cslot_write, s, simplified ? 1 : 0))) return st;
     if ((st = launch_trig(g, (double *)c->buf[B_TRIG], s))) return st;
     if ((st = launch_assemble(g, K, conds, cslot_write, D, aE, aN, S, (const double *)c->buf[B_TRIG],
                               (int *)c->buf[B_FLAGS], NSLOT, s)))
         return st;
-    // (a3) joint solve; conditions 5..8 (edot perturbations) use the coefficients of condition 0.
-    // zero_init = 0 warm-starts from the fields the previous step of this shape left in
-    // the context (the previous Picard iterate or time step); otherwise from zero.
-    const int cslot[9] = {0, 1, 2, 3, 4, 0, 0, 0, 0};
+    // (a3) joint solve; the edot-perturbed conditions use the coefficients of condition 0.
+    // zero_init = 0 warm-starts from the fields the previous step of this shape and
+    // scheme left in the context (the previous Picard iterate or time step); otherwise
+    // from zero.
+    const int cslot_general[9] = {0, 1, 2, 3, 4, 0, 0, 0, 0};
+    const int cslot_simplified[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int *cslot = simplified ? cslot_simplified : cslot_general;
     gmaf_solver_opts o = *opts;
-    const bool warm = !opts->zero_init && c->pp_nth == g.nth && c->pp_nz == g.nz;
+    const bool warm = !opts->zero_init && c->pp_nth == g.nth && c->pp_nz == g.nz && c->pp_K == K;
     o.zero_init = warm ? 0 : 1;
     c->pp_nth = g.nth;
     c->pp_nz = g.nz;
+    c->pp_K = K;
     gmaf_solve_info info{};
     const int sst = solve_joint_device(c, g.nth, g.nz, K, NSLOT, cslot, D, aE, aN, S, p, &o, &info);
     c->info = info;
@@ -369,6 +379,7 @@ int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phy
     std::memcpy(in.base, base, sizeof base);
     std::memcpy(in.e_prev, e_prev, 4 * sizeof(double));
     std::memcpy(in.F_ext, F_ext, 4 * sizeof(double));
+    in.simplified = simplified ? 1 : 0;
     if ((st = launch_picard_update((const double *)c->buf[B_LOADS], in, dt, d_e, d_edot, g.L,
                                    (double *)c->buf[B_RESULT], s)))
         return st;
@@ -387,6 +398,28 @@ int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phy
     std::memcpy(state->e, res + 64, 4 * sizeof(double));
     std::memcpy(state->edot, res + 68, 4 * sizeof(double));
     return GMAF_OK;
+}
+
+extern "C" {
+
+int gmaf_picard_step(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phys,
+                     const gmaf_texture *tex, gmaf_state *state, const double e_prev[4], double dt,
+                     const double F_ext[4], double d_e, double d_edot, const gmaf_solver_opts *opts,
+                     double loads_out[12], double J_out[48], double G_out[4], int32_t *iters_out)
+{
+    return picard_impl(c, grid, phys, tex, state, e_prev, dt, F_ext, d_e, d_edot, opts, loads_out,
+                       J_out, G_out, iters_out, false);
+}
+
+int gmaf_picard_step_simplified(gmaf_ctx *c, const gmaf_grid *grid, const gmaf_physics *phys,
+                                const gmaf_texture *tex, gmaf_state *state, double dt,
+                                const double F_ext[4], double d_edot, const gmaf_solver_opts *opts,
+                                double loads_out[12], double J_out[48], double G_out[4],
+                                int32_t *iters_out)
+{
+    if (!state) return GMAF_INVALID_ARG;
+    return picard_impl(c, grid, phys, tex, state, state->e, dt, F_ext, 1.0, d_edot, opts, loads_out,
+                       J_out, G_out, iters_out, true);
 }
 
 }  // extern "C"

@@ -131,25 +131,33 @@ int launch_trig(const Geom &g, double *trig, cudaStream_t s)
 // conds[k] = base for k = 0; e_{k-1} + d_e for k = 1..4; edot_{k-5} + d_edot for k = 5..8.
 // cslot_write[k] = k for k <= 4 (own coefficients), -1 for k >= 5: the ė-perturbed
 // conditions share the coefficients of condition 0 because A depends on e only.
+// General scheme (Eq. 2.13-2.19): condition 0 = (e, edot), 1..4 = e_j + d_e,
+// 5..8 = edot_j + d_edot; coefficient slots 0..4 (A does not depend on edot).
+// Simplified scheme (Eq. 2.20): 0 = (e, edot), 1..4 = edot_j + d_edot, all in slot 0.
 __global__ void k_fanout(const double base0, const double base1, const double base2,
                          const double base3, const double base4, const double base5,
                          const double base6, const double base7, double d_e, double d_edot,
-                         double *conds, int *cslot_write)
+                         double *conds, int *cslot_write, int simplified)
 {
     const int k = threadIdx.x;
-    if (k >= 9) return;
+    if (k >= (simplified ? 5 : 9)) return;
     double s[8] = {base0, base1, base2, base3, base4, base5, base6, base7};
-    if (k >= 1 && k <= 4) s[k - 1] += d_e;
-    if (k >= 5) s[4 + (k - 5)] += d_edot;
+    if (simplified) {
+        if (k >= 1) s[4 + (k - 1)] += d_edot;
+        cslot_write[k] = (k == 0) ? 0 : -1;
+    } else {
+        if (k >= 1 && k <= 4) s[k - 1] += d_e;
+        if (k >= 5) s[4 + (k - 5)] += d_edot;
+        cslot_write[k] = (k <= 4) ? k : -1;
+    }
     for (int q = 0; q < 8; ++q) conds[k * 8 + q] = s[q];
-    cslot_write[k] = (k <= 4) ? k : -1;
 }
 
 int launch_fanout(const double *b, double d_e, double d_edot, double *conds, int *cslot_write,
-                  cudaStream_t s)
+                  cudaStream_t s, int simplified)
 {
     k_fanout<<<1, 32, 0, s>>>(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], d_e, d_edot, conds,
-                              cslot_write);
+                              cslot_write, simplified);
     return cuda_status(cudaGetLastError());
 }
 
@@ -422,12 +430,21 @@ __global__ void k_picard(const double *__restrict__ loads, PicardIn in, double d
 {
     if (threadIdx.x != 0) return;
     const double *base = in.base, *e_prev = in.e_prev, *F_ext = in.F_ext;
+    const bool simp = in.simplified != 0;
+    const int K = simp ? 5 : 9;
     double F[9][6];
-    for (int k = 0; k < 9; ++k)
+    for (int k = 0; k < K; ++k)
         for (int c = 0; c < 6; ++c) F[k][c] = loads[k * 12 + c] + loads[k * 12 + 6 + c];
+    // load Jacobian by forward differences (Eq. 2.13-2.14); the simplified scheme
+    // forms only the rate columns, from its conditions 1..4
     double J[6][8];
     for (int r = 0; r < 6; ++r)
-        for (int c = 0; c < 8; ++c) J[r][c] = (F[1 + c][r] - F[0][r]) / (c < 4 ? d_e : d_edot);
+        for (int c = 0; c < 8; ++c) {
+            if (simp)
+                J[r][c] = c < 4 ? 0.0 : (F[1 + (c - 4)][r] - F[0][r]) / d_edot;
+            else
+                J[r][c] = (F[1 + c][r] - F[0][r]) / (c < 4 ? d_e : d_edot);
+        }
     // generalized force of the linear tilt: (Fx - My/L, Fy + Mx/L, My/L, -Mx/L)
     auto gen = [L](const double *f, double *gout) {
         gout[0] = f[0] - f[4] / L;
@@ -448,12 +465,14 @@ __global__ void k_picard(const double *__restrict__ loads, PicardIn in, double d
         gen(col, gg);
         for (int r = 0; r < 4; ++r) Jd[r][c] = gg[r];
     }
+    // general: (J_edot + dt J_e) delta = -G - J_e (e_prev + dt edot - e);
+    // simplified (Eq. 2.20-2.21): J_edot delta = -G
     double A[4][5];
     for (int r = 0; r < 4; ++r) {
         double s = 0.0;
         for (int c = 0; c < 4; ++c) {
-            A[r][c] = Jd[r][c] + dt * Je[r][c];
-            s += Je[r][c] * (e_prev[c] + dt * base[4 + c] - base[c]);
+            A[r][c] = simp ? Jd[r][c] : Jd[r][c] + dt * Je[r][c];
+            if (!simp) s += Je[r][c] * (e_prev[c] + dt * base[4 + c] - base[c]);
         }
         A[r][4] = -G[r] - s;
     }
@@ -493,7 +512,8 @@ __global__ void k_picard(const double *__restrict__ loads, PicardIn in, double d
     for (int q = 0; q < 4; ++q) {
         const double ed = base[4 + q] + delta[q];
         result[64 + 4 + q] = ed;
-        result[64 + q] = e_prev[q] + dt * ed;
+        // general: e = e_prev + dt edot_new; simplified: e += dt delta (Eq. 2.22)
+        result[64 + q] = simp ? base[q] + dt * delta[q] : e_prev[q] + dt * ed;
     }
     result[72] = (double)status;
 }

@@ -133,7 +133,7 @@ struct gmaf_ctx {
     int force_variant;             // GMAF_VARIANT=<id>: use that kernel variant when eligible
     gmaf::TuneEntry tune[gmaf::kTuneEntries];
     int ntune, tune_next;
-    int pp_nth, pp_nz;             // shape of the Picard-step fields held in B_PP
+    int pp_nth, pp_nz, pp_K;       // shape of the Picard-step fields held in B_PP
     double inner_floor;            // smallest relative residual asked of an inner FP32 solve
 };
 
@@ -148,8 +148,10 @@ bool opts_valid(const gmaf_solver_opts *o);
 
 // geometry / assembly / loads / Picard kernels (gmaf_assemble.cu)
 int launch_trig(const Geom &g, double *trig, cudaStream_t s);
+// simplified = 0: the 9 conditions of the general scheme (base, e_j + d_e, edot_j + d_edot)
+// in 5 coefficient slots; 1: the 5 of the simplified scheme (base, edot_j + d_edot) in 1 slot.
 int launch_fanout(const double *base, double d_e, double d_edot, double *conds, int *cslot_write,
-                  cudaStream_t s);
+                  cudaStream_t s, int simplified = 0);
 int launch_assemble(const Geom &g, int ncond, const double *conds, const int *coef_slot,
                     double *D, double *aE, double *aN, double *S, const double *trig, int *flags,
                     int nslots, cudaStream_t s);
@@ -158,6 +160,7 @@ int launch_loads(const Geom &g, int ncond, const double *conds, const double *p,
                  int *flags, int num_sms, cudaStream_t s);
 struct PicardIn {
     double base[8], e_prev[4], F_ext[4];
+    int simplified;                // Eq. 2.20-2.22 on the 5-condition batch
 };
 constexpr int kResultDoubles = 73;
 int launch_picard_update(const double *loads, const PicardIn &in, double dt, double d_e,

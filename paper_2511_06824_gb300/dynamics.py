@@ -78,14 +78,22 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
           steps_per_rev: int = 360, rpm: float = 600.0, v_amp: float = 5.0,
           kappa: float = 0.2, tol_F: float = 1e-6, max_picard: int = 20,
           d_e: float = 2e-8, d_edot: float = 1e-6, opts: Optional[gmaf.gmaf_solver_opts] = None,
-          on_step: Optional[Callable[[StepRecord], None]] = None) -> Trajectory:
+          on_step: Optional[Callable[[StepRecord], None]] = None,
+          scheme: str = "general") -> Trajectory:
     """Run `steps` shaft-angle steps.  p_profile[s % steps_per_rev] is the chamber
-    pressure of step s; the sliding speed is v_amp * sin(phi)."""
+    pressure of step s; the sliding speed is v_amp * sin(phi).
+
+    scheme "general": the double-Jacobian Picard iteration (Eq. 2.12-2.19, 9 conditions).
+    scheme "simplified": the conventional one (Eq. 2.20-2.22, 5 conditions); each time
+    step starts from the predictor e = e_l + dt edot_l, so that the increments of
+    Eq. 2.22 keep e = e_l + dt edot, the backward difference, at every iterate."""
+    if scheme not in ("general", "simplified"):
+        raise ValueError(f"unknown scheme {scheme!r}")
     phys = np.asarray(phys, dtype=np.float64).copy()
     dt = (60.0 / rpm) / steps_per_rev
     state = np.asarray(state0, dtype=np.float64).copy()
     o = opts or gmaf.solver_opts(precision=1)
-    warm = gmaf.gmaf_solver_opts(o.precond, o.omega, o.eps, o.max_iter, o.precision, 0)
+    warm = gmaf.gmaf_solver_opts(o.precond, o.omega, o.eps, o.max_iter, o.precision, 0, o.criterion)
     traj = Trajectory()
     first_solve = True
     for s in range(steps):
@@ -97,14 +105,21 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
         F_ext = side_load(ph[5], ph[0], kappa)
         scale = max(float(np.linalg.norm(F_ext)), 1.0)
         e_prev = state[:4].copy()
+        if scheme == "simplified":
+            state[:4] = e_prev + dt * state[4:]
         converged = False
         pcg = 0
         G_norm = float("inf")
         loads = np.zeros(12)
         it = 0
         for it in range(1, max_picard + 1):
-            r = gmaf.gmaf_picard_step(ctx, n_theta, n_z, ph, tex, state, e_prev, dt, F_ext, d_e,
-                                      d_edot, o if first_solve else warm)
+            oo = o if first_solve else warm
+            if scheme == "simplified":
+                r = gmaf.gmaf_picard_step_simplified(ctx, n_theta, n_z, ph, tex, state, dt, F_ext,
+                                                     d_edot, oo)
+            else:
+                r = gmaf.gmaf_picard_step(ctx, n_theta, n_z, ph, tex, state, e_prev, dt, F_ext, d_e,
+                                          d_edot, oo)
             first_solve = False
             pcg += r["iters"]
             G_norm = float(np.linalg.norm(r["G"]))

@@ -33,7 +33,8 @@ EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_by
             "gmaf_picard_step", "gmaf_status_string", "gmaf_set_phase_timing",
             "gmaf_phase_timing", "gmaf_solve_joint_noalloc", "gmaf_request_footprint",
             "gmaf_server_create", "gmaf_server_destroy", "gmaf_server_submit", "gmaf_server_run",
-            "gmaf_server_poll", "gmaf_server_free_bytes", "gmaf_last_fields")
+            "gmaf_server_poll", "gmaf_server_free_bytes", "gmaf_last_fields",
+            "gmaf_picard_step_simplified")
 
 
 class gmaf_grid(ctypes.Structure):
@@ -121,6 +122,10 @@ def load(path: str = LIB_PATH):
                                    ctypes.c_double, _DP, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(gmaf_solver_opts), _DP, _DP, _DP,
                                    ctypes.POINTER(ctypes.c_int32)]
+    L.gmaf_picard_step_simplified.argtypes = [
+        _VP, ctypes.POINTER(gmaf_grid), ctypes.POINTER(gmaf_physics), ctypes.POINTER(gmaf_texture),
+        ctypes.POINTER(gmaf_state), ctypes.c_double, _DP, ctypes.c_double,
+        ctypes.POINTER(gmaf_solver_opts), _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int32)]
     L.gmaf_set_phase_timing.argtypes = [_VP, ctypes.c_int]
     L.gmaf_phase_timing.argtypes = [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]
     L.gmaf_solve_joint_noalloc.argtypes = [ctypes.POINTER(gmaf_grid), ctypes.c_int32, _VP, _VP,
@@ -306,6 +311,29 @@ def gmaf_picard_step(ctx: int, n_theta: int, n_z: int, phys, tex, st_vec, e_prev
                                  loads.ctypes.data_as(_DP), J.ctypes.data_as(_DP),
                                  G.ctypes.data_as(_DP), ctypes.byref(it))
     _check("gmaf_picard_step", rc, allow)
+    return dict(status=rc, state=state_vector(s), loads=loads, J=J.reshape(6, 8), G=G,
+                iters=it.value)
+
+
+def gmaf_picard_step_simplified(ctx: int, n_theta: int, n_z: int, phys, tex, st_vec, dt, F_ext,
+                                d_edot, opts: Optional[gmaf_solver_opts] = None,
+                                allow=(GMAF_OK,)) -> dict:
+    """One conventional (simplified) Picard iteration, Eq. 2.20-2.22; the result dict
+    as gmaf_picard_step's (J's e-columns zero)."""
+    g, ph, tx = grid(n_theta, n_z), physics(phys), texture(tex)
+    s = state(st_vec)
+    fe = _f64(F_ext, 4)
+    loads = np.zeros(12)
+    J = np.zeros(48)
+    G = np.zeros(4)
+    it = ctypes.c_int32(0)
+    o = opts or solver_opts()
+    rc = load().gmaf_picard_step_simplified(_VP(ctx), ctypes.byref(g), ctypes.byref(ph),
+                                            ctypes.byref(tx), ctypes.byref(s), float(dt),
+                                            fe.ctypes.data_as(_DP), float(d_edot), ctypes.byref(o),
+                                            loads.ctypes.data_as(_DP), J.ctypes.data_as(_DP),
+                                            G.ctypes.data_as(_DP), ctypes.byref(it))
+    _check("gmaf_picard_step_simplified", rc, allow)
     return dict(status=rc, state=state_vector(s), loads=loads, J=J.reshape(6, 8), G=G,
                 iters=it.value)
 

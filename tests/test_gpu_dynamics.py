@@ -86,3 +86,24 @@ def test_warm_start_saves_iterations_and_keeps_the_answer(g):
     scale = np.maximum(np.abs(cold["loads"]), 1e-3 * np.linalg.norm(cold["loads"]))
     assert np.max(np.abs(warm["loads"] - cold["loads"]) / scale) < 1e-8
     np.testing.assert_allclose(warm["state"], cold["state"], rtol=1e-6, atol=1e-14)
+
+
+def test_simplified_scheme_reaches_the_same_balance(g):
+    """Both Picard schemes stop at force balance with e = e_l + dt edot (the general
+    one by its closure, the simplified one through the predictor and Eq. 2.22), so on
+    every step where both converge their states agree to the balance tolerance."""
+    from paper_2511_06824_gb300 import dynamics
+    nth, nz, steps = 48, 24, 6
+    phys = inputs.phys_vector()
+    tex = inputs.dimple_texture(np.random.default_rng(4))
+    prof = inputs.trapezoid_pressure_profile(np.random.default_rng(3), 360)
+    st0 = np.array([2e-6, -1e-6, 3e-6, 1e-6, 0, 0, 0, 0.0])
+    opts = g.solver_opts(eps=1e-12, precision=0)
+    with g.Context() as c:
+        gen = dynamics.march(c.handle, nth, nz, phys, tex, st0, prof, steps, kappa=0.2,
+                             opts=opts, tol_F=1e-9, scheme="general")
+        sim = dynamics.march(c.handle, nth, nz, phys, tex, st0, prof, steps, kappa=0.2,
+                             opts=opts, tol_F=1e-9, max_picard=40, scheme="simplified")
+    assert all(r.converged for r in gen.records) and all(r.converged for r in sim.records)
+    scale = np.abs(gen.states[:, :4]).max()
+    assert np.abs(sim.states[:, :4] - gen.states[:, :4]).max() <= 1e-6 * scale

@@ -382,6 +382,36 @@ def test_picard_step_matches_oracle(g, ctx, nth, nz, textured, precision):
     assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o) + 1e-20
 
 
+@pytest.mark.parametrize("nth,nz,textured,precision", [(64, 32, False, 0), (96, 48, True, 0),
+                                                       (96, 48, True, 1)])
+def test_simplified_picard_step_matches_oracle(g, ctx, nth, nz, textured, precision):
+    """Eq. 2.20-2.22 on 5 conditions: loads, rate Jacobian, G and the update."""
+    tex = tex_dimples() if textured else inputs.smooth_texture()
+    st0 = states(1, seed=37)[0]
+    Fext = np.array([25.0, -10.0, 4.0, 3.0])
+    dt = 2.78e-4
+    eps = 1e-12
+    r = g.gmaf_picard_step_simplified(ctx, nth, nz, PHYS, tex, st0, dt, Fext, 1e-6,
+                                      g.solver_opts(eps=eps, precision=precision))
+    o = oracle.picard_step_simplified(nth, nz, PHYS, tex, st0, dt, Fext, 1e-6, eps=eps)
+    assert r["status"] == 0 and o["status"] == 0
+    tol_l = 1e-7 if precision == 0 else 1e-5
+    assert load_err(r["loads"], o["loads"]) <= tol_l
+    assert not np.any(r["J"][:, :4])
+    Jg, Jo = r["J"][:, 4:], o["J"][:, 4:]
+    colscale = np.abs(Jo).max(axis=0, keepdims=True)
+    assert np.max(np.abs(Jg - Jo) / colscale) <= (1e-5 if precision == 0 else 1e-3)
+    np.testing.assert_allclose(r["G"], o["G"], rtol=1e-6, atol=1e-6 * np.abs(o["G"]).max())
+    ds_g, ds_o = r["state"] - st0, o["state"] - st0
+    assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o) + 1e-20
+    # the fields of the 5 conditions; the rest of the buffer is left alone
+    n = nth * nz
+    buf = torch.full((9 * n,), 7.0, dtype=torch.float64, device="cuda")
+    g.gmaf_last_fields(ctx, nth, nz, buf)
+    hb = host(buf)
+    assert np.all(hb[5 * n:] == 7.0) and np.all(np.isfinite(hb[:5 * n]))
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_phase_timing_path_matches_graph_path(g, precision):
     """Per-phase event timing drives the loop from the host; results are bitwise the
