@@ -133,6 +133,11 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     c->budget = hbm_budget_bytes;
     const char *ng = std::getenv("GMAF_NO_GRAPH");
     c->no_graph = (ng && ng[0] == '1') ? 1 : 0;
+    const char *gp = std::getenv("GMAF_GRAPH_UNROLL");
+    // 4 PCG iterations per evaluation of the graph's loop condition: each evaluation
+    // costs about 4 us on the 2048 x 1024 x 9 step (0.2245 -> 0.2214 ms per iteration)
+    c->graph_pairs = gp ? std::atoi(gp) : 4;
+    if (c->graph_pairs < 1 || c->graph_pairs > 8) c->graph_pairs = 4;
     const char *nt = std::getenv("GMAF_NO_TUNE");
     c->no_tune = (nt && nt[0] == '1') ? 1 : 0;
     const char *fv = std::getenv("GMAF_VARIANT");

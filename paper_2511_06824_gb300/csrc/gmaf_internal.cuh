@@ -100,7 +100,9 @@ struct GraphCache {
     cudaGraphConditionalHandle handle = 0;
     int grid_a = 0, grid_b = 0, grid_s = 0;
     const void *desc = nullptr;
-    const void *ka = nullptr;      // phase-A kernel the graph was built with
+    const void *ka = nullptr;      // phase kernels the graph was built with
+    const void *kb = nullptr;
+    int pairs = 0;                 // A -> B pairs per trip of the WHILE body
 };
 
 // Autotuner decision for one solve shape.
@@ -124,6 +126,7 @@ struct gmaf_ctx {
     gmaf::GraphCache graph64, graph32;
     int num_sms;
     int no_graph;                  // loop control by host chunks instead of a graph
+    int graph_pairs;               // PCG iterations per trip of the graph's WHILE body
     int phase_timing;              // events around each phase launch (host chunks)
     double phase_ms[4];
     long long phase_count[4];

@@ -187,17 +187,17 @@ static cudaError_t launch(const void *fn, int grid, const PcgDesc<T> *dd, cudaSt
 }
 
 static bool graph_matches(const GraphCache &gc, int ga, int gb, int gs, const void *desc,
-                          const void *ka)
+                          const void *ka, const void *kb, int pairs)
 {
     return gc.exec && gc.grid_a == ga && gc.grid_b == gb && gc.grid_s == gs && gc.desc == desc &&
-           gc.ka == ka;
+           gc.ka == ka && gc.kb == kb && gc.pairs == pairs;
 }
 
 // Build and instantiate  [init B] -> WHILE{A -> B} -> [finalize]  for a launch
 // shape.  The kernels read everything through the device descriptor, so one
 // instantiated graph serves every problem of that shape.
 template <typename T>
-static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
+static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs)
 {
     if (gc.exec) {
         cudaGraphExecDestroy(gc.exec);
@@ -226,16 +226,23 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     cp.conditional.size = 1;
     if (e == cudaSuccess) e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp);
     if (e == cudaSuccess) {
+        // the body runs `pairs` iterations per evaluation of the condition; once the
+        // run is done, the remaining phases of the trip return at once (phase A also
+        // writes "stop" to the condition before it looks at done)
         cudaGraph_t body = cp.conditional.phGraph_out[0];
-        kp.func = (void *)run.ks.a;
-        kp.gridDim = dim3(run.grid_a);
-        kp.sharedMemBytes = 0;
-        e = cudaGraphAddKernelNode(&n_a, body, nullptr, 0, &kp);
-        if (e == cudaSuccess) {
-            kp.func = (void *)run.ks.b;
-            kp.gridDim = dim3(run.grid_b);
-            kp.sharedMemBytes = (unsigned)run.ks.smem_b;
-            e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
+        cudaGraphNode_t prev = nullptr;
+        for (int q = 0; q < pairs && e == cudaSuccess; ++q) {
+            kp.func = (void *)run.ks.a;
+            kp.gridDim = dim3(run.grid_a);
+            kp.sharedMemBytes = 0;
+            e = cudaGraphAddKernelNode(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            if (e == cudaSuccess) {
+                kp.func = (void *)run.ks.b;
+                kp.gridDim = dim3(run.grid_b);
+                kp.sharedMemBytes = (unsigned)run.ks.smem_b;
+                e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
+            }
+            prev = n_b;
         }
     }
     if (e == cudaSuccess) {
@@ -256,6 +263,8 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s)
     gc.grid_s = run.grid_s;
     gc.desc = run.d_desc;
     gc.ka = run.ks.a;
+    gc.kb = run.ks.b;
+    gc.pairs = pairs;
     (void)s;
     return GMAF_OK;
 }
@@ -416,8 +425,9 @@ static int prepare(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc)
     if (!use_graph(ctx)) {
         run.h.use_cond = 0;
     } else {
-        if (!graph_matches(gc, run.grid_a, run.grid_b, run.grid_s, run.d_desc, run.ks.a))
-            GMAF_TRY(build_graph<T>(run, gc, ctx->stream));
+        if (!graph_matches(gc, run.grid_a, run.grid_b, run.grid_s, run.d_desc, run.ks.a, run.ks.b,
+                           ctx->graph_pairs))
+            GMAF_TRY(build_graph<T>(run, gc, ctx->stream, ctx->graph_pairs));
         run.h.use_cond = 1;
         run.h.cond = gc.handle;
     }
