@@ -182,6 +182,21 @@ def ncu_traffic(workload: str, precision: str, variant: int, kernel: str):
 # ----------------------------------------------------------------------------- our arm
 
 
+def replica_totals(ms: float, work: float, dist) -> tuple:
+    """Whole-job figures of the replicas (one per GPU, no exchange on the data path):
+    the slowest rank's time and the work summed over ranks, so that the throughput
+    is sum(work) / max(time).  dist is torch.distributed (None on one GPU)."""
+    if dist is None:
+        return ms, work
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([work], dtype=torch.float64, device=dev)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(v.item())
+
+
 def run_ours(args):
     import torch
 
@@ -238,16 +253,12 @@ def run_ours(args):
         barrier()
         clocks = sampler.stop() if sampler else None
         ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
         return ms, its, outer, clocks
 
     opts = gmaf.solver_opts(precond=1, omega=w.omega, eps=w.eps, precision=prec)
     K, W = args.steps, max(3, args.warmup)
     ms, its, outer, clocks = timed(opts, K, W, True)
-    total_dof_iter = float(sum(its)) * w.dof * world
+    ms, total_dof_iter = replica_totals(ms, float(sum(its)) * w.dof, dist)
     value = total_dof_iter / (ms / 1e3)
     picard_rate = K * world / (ms / 1e3)
 
@@ -275,11 +286,7 @@ def run_ours(args):
         gmaf.gmaf_picard_step(ctx.handle, w.n_theta, w.n_z, w.phys, w.tex, host_in[:8],
                               host_in[8:12], DT, host_in[12:16], w.d_e, w.d_edot, opts)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e, _ = replica_totals(time.perf_counter() - t0, 0.0, dist)
     structs = sum(ctypes.sizeof(c) for c in (gmaf.gmaf_grid, gmaf.gmaf_physics,
                                               gmaf.gmaf_texture, gmaf.gmaf_solver_opts))
     h2d = 16 * 8 + 3 * 8 + structs
@@ -323,7 +330,7 @@ def run_ours(args):
         "pcg_iterations_per_step": float(np.mean(its)),
         "outer_refinements_per_step": float(np.mean(outer)),
         "kernel_variant": timed.info["kernel_variant"], "tasks_per_phase": timed.info["tasks"],
-        "e2e": {"value": float(sum(its)) * w.dof * world / t_e2e, "unit": UNIT,
+        "e2e": {"value": total_dof_iter / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "picard_steps_per_s": K * world / t_e2e},
         "gpu_launches": gpu_launches,
@@ -336,6 +343,7 @@ def run_ours(args):
         o64 = gmaf.solver_opts(precond=1, omega=w.omega, eps=w.eps, precision=0)
         K64 = 2
         ms64, its64, _, _ = timed(o64, K64, 1, False)
+        ms64, tot64 = replica_totals(ms64, float(sum(its64)) * w.dof, dist)
         gmaf.gmaf_set_phase_timing(ctx.handle, True)
         step(o64)
         ph64 = gmaf.gmaf_phase_timing(ctx.handle)
@@ -348,7 +356,7 @@ def run_ours(args):
             gbs = b64[k] * w.dof / (avg / 1e3) / 1e9
             p64[k] = {"avg_ms": avg, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm}
         out["fp64"] = {"ms_per_step": ms64 / K64,
-                       "value": float(sum(its64)) * w.dof * world / (ms64 / 1e3),
+                       "value": tot64 / (ms64 / 1e3),
                        "picard_steps_per_s": K64 * world / (ms64 / 1e3),
                        "pcg_iterations_per_step": float(np.mean(its64)), "phases": p64,
                        "kernel_variant": timed.info["kernel_variant"],
