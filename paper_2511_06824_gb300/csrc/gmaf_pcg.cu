@@ -111,14 +111,16 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
 {
     int n = 0;
     if (vec_ok) {
+        // 32-row tasks suit the largest grids; 16 and 8 rows and the static
+        // schedule keep every warp busy on smaller ones (1024 x 512 x 9 has only
+        // 1152 tasks of 32 rows for 2432 resident warps)
         out[n++] = ks_of<float, 4, 32, 2>(0);
         out[n++] = ks_staged<float, 4, 32, 2, 2>();
-        out[n++] = ks_staged<float, 4, 32, 3, 2>();
-        out[n++] = ks_staged<float, 4, 16, 3, 2>();
+        out[n++] = ks_staged<float, 4, 16, 2, 2>();
         out[n++] = ks_of<float, 4, 16, 2>(0);
+        out[n++] = ks_of<float, 4, 8, 2>(0);
         out[n++] = ks_of<float, 2, 32, 4>(2);
         out[n++] = ks_of<float, 4, 32, 2, 1>(0);
-        out[n++] = ks_of<float, 2, 32, 4, 1>(0);
     }
     if (vec8_ok) out[n++] = ks_staged<float, 8, 32, 2, 1>();
     out[n++] = ks_of<float, 1, 32, 4>(4);

@@ -233,7 +233,8 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
 # marching against phase B (ids 1000000 + 1000 VEC + MINB); float VEC > 1 kernels
 # need n_theta % 4 == 0, double ones an even n_theta
 @pytest.mark.parametrize("precision,variant,nth,nz,K", [
-    (1, 4322, 132, 45, 9), (1, 1004002, 132, 45, 9), (1, 1002004, 260, 33, 4),
+    (1, 4322, 132, 45, 9), (1, 1004002, 132, 45, 9), (1, 4082, 260, 33, 4),
+    (1, 204162, 132, 45, 9), (1, 204322, 260, 70, 3),
     (1, 1001004, 131, 7, 3), (0, 2322, 130, 45, 9), (0, 1002002, 130, 45, 9),
     (0, 1001003, 131, 7, 3), (0, 1001003, 3, 2, 1),
 ])
