@@ -138,6 +138,9 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     // costs about 4 us on the 2048 x 1024 x 9 step (0.2245 -> 0.2214 ms per iteration)
     c->graph_pairs = gp ? std::atoi(gp) : 4;
     if (c->graph_pairs < 1 || c->graph_pairs > 8) c->graph_pairs = 4;
+    const char *cf = std::getenv("GMAF_CHUNKED_FROM");
+    c->chunked_from = cf ? std::atoll(cf) : 4096;
+    if (c->chunked_from < 1) c->chunked_from = 4096;
     const char *nt = std::getenv("GMAF_NO_TUNE");
     c->no_tune = (nt && nt[0] == '1') ? 1 : 0;
     const char *fv = std::getenv("GMAF_VARIANT");

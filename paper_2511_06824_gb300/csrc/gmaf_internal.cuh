@@ -65,6 +65,8 @@ struct PcgDesc {
     cudaGraphConditionalHandle cond;
     Scalars *sc;
     double *partials;              // per-task (or per-warp) sums [ntiles][2], or per-block [2][grid]
+    double *chunk_sum;             // two-level reduction: chunk sums [chunks][2] (nullptr: one level)
+    unsigned *chunk_ctr;           // per-chunk counters, zero between launches
 };
 
 // FP64 residual r = S - A p over all conditions, with ||r||^2 and ||S||^2.
@@ -92,6 +94,8 @@ enum BufId {
     B_R64,
     // asynchronized criterion: per-condition descriptors
     B_ASYNC,
+    // two-level reduction of the phase kernels: chunk sums, chunk counters
+    B_CHUNK, B_CHUNKCTR,
     B_COUNT
 };
 
@@ -127,6 +131,7 @@ struct gmaf_ctx {
     int num_sms;
     int no_graph;                  // loop control by host chunks instead of a graph
     int graph_pairs;               // PCG iterations per trip of the graph's WHILE body
+    long long chunked_from;        // two-level reduction from this many publishing units
     int phase_timing;              // events around each phase launch (host chunks)
     double phase_ms[4];
     long long phase_count[4];

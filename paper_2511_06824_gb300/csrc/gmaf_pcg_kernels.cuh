@@ -290,6 +290,19 @@ __device__ __forceinline__ unsigned next_task(unsigned *ctr, int lane)
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
+// Where a phase launch publishes its sums.
+struct PcgReduce {
+    double *partials;
+    double *chunk_sum;
+    unsigned *chunk_ctr;
+};
+
+template <typename T>
+__device__ __forceinline__ PcgReduce reducer_of(const PcgDesc<T> &d)
+{
+    return PcgReduce{d.partials, d.chunk_sum, d.chunk_ctr};
+}
+
 // Publish NV per-task sums (warp-reduced in a fixed order) at partials[t * NV + q].
 template <int NV>
 __device__ __forceinline__ void publish_task(const double (&v)[NV], double *partials, unsigned t,
@@ -303,10 +316,11 @@ __device__ __forceinline__ void publish_task(const double (&v)[NV], double *part
 }
 
 // After every task of the launch is published: the last block (by ticket)
-// adds the per-task sums in task order, so the totals depend neither on the
-// grid nor on which warp ran which task.  Also rearms the task counter.
+// adds the n sums (entry i's q-th at sums[i * stride + q]) in entry order, so
+// the totals depend neither on the grid nor on which warp ran which task.
+// Also rearms the task counter.
 template <int NV>
-__device__ __forceinline__ bool reduce_tasks(const double *partials, unsigned ntasks,
+__device__ __forceinline__ bool reduce_tasks(const double *sums, unsigned n, int stride,
                                              unsigned *ticket, unsigned *task_ctr,
                                              double (&tot)[NV])
 {
@@ -322,15 +336,15 @@ __device__ __forceinline__ bool reduce_tasks(const double *partials, unsigned nt
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    // each thread adds the partials of tasks threadIdx.x, + blockDim.x, ... in
-    // that order; the unrolled loop keeps several L2 loads in flight
+    // each thread adds the entries threadIdx.x, + blockDim.x, ... in that order;
+    // the unrolled loop keeps several L2 loads in flight
     double acc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = 0.0;
 #pragma unroll 4
-    for (unsigned t = threadIdx.x; t < ntasks; t += blockDim.x) {
+    for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&partials[(size_t)t * NV + q]);
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&sums[(size_t)t * stride + q]);
     }
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -349,6 +363,51 @@ __device__ __forceinline__ bool reduce_tasks(const double *partials, unsigned nt
         *task_ctr = 0u;
     }
     return true;
+}
+
+// Two-level reduction.  The publishing units (tasks, or warps under the static
+// schedule) form chunks of kChunk consecutive ids.  A unit publishes its sums
+// and counts itself in its chunk; the warp that completes a chunk adds the
+// chunk's sums (a fixed butterfly over the units in id order), stores the chunk
+// sum and rearms the counter.  The last block then adds only the chunk sums, in
+// chunk order: the same determinism as one level, and the serial work left after
+// the last task shrinks from one sum per unit (adds on one SM's FP64 pipe) to
+// one per chunk.
+constexpr int kChunk = 32;
+
+template <int NV>
+__device__ __forceinline__ void publish_unit(const double (&v)[NV], const PcgReduce &rd,
+                                             unsigned units, unsigned t, int lane)
+{
+    publish_task<NV>(v, rd.partials, t, lane);
+    if (!rd.chunk_sum) return;
+    const unsigned c = t / kChunk;
+    const unsigned cnt = min((unsigned)kChunk, units - c * kChunk);
+    unsigned prev = 0;
+    if (lane == 0) {
+        __threadfence();
+        prev = atomicAdd(&rd.chunk_ctr[c], 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != cnt - 1) return;
+    __threadfence();
+    const unsigned u = c * kChunk + (unsigned)lane;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const double x = warp_sum_d((unsigned)lane < cnt ? __ldcg(&rd.partials[(size_t)u * NV + q]) : 0.0);
+        if (lane == 0) rd.chunk_sum[(size_t)c * 2 + q] = x;
+    }
+    if (lane == 0) rd.chunk_ctr[c] = 0u;
+}
+
+// The last block's totals: over the chunk sums, or (one level) the unit sums.
+template <int NV>
+__device__ __forceinline__ bool reduce_units(const PcgReduce &rd, unsigned units, unsigned *ticket,
+                                             unsigned *task_ctr, double (&tot)[NV])
+{
+    if (rd.chunk_sum)
+        return reduce_tasks<NV>(rd.chunk_sum, (units + kChunk - 1) / kChunk, 2, ticket, task_ctr, tot);
+    return reduce_tasks<NV>(rd.partials, units, NV, ticket, task_ctr, tot);
 }
 
 // ------------------------------------------------------------------ phase A
@@ -553,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
             const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
             const double val[1] = {run_task_a<T, VEC, false>(d, tk, s_k, s_first != 0, (T)s_alpha,
                                                               (T)s_beta, su[wp], sa[wp], lane)};
-            publish_task<1>(val, d.partials, t, lane);
+            publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
         }
     } else {
         ntasks = gridDim.x * kWarps;
@@ -564,10 +623,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
                                           sa[wp], lane);
         });
         const double val[1] = {v};
-        publish_task<1>(val, d.partials, gw, lane);
+        publish_unit<1>(val, reducer_of(d), ntasks, gw, lane);
     }
     double tot[1];
-    if (reduce_tasks<1>(d.partials, ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
+    if (reduce_units<1>(reducer_of(d), ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
         threadIdx.x == 0)
         finish_a(sc, tot[0]);
 }
@@ -850,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__
             const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
             double val[2];
             run_task_b<T, VEC, INIT>(d, tk, s_k, (T)s_alpha, sy[wp], sw[wp], sa[wp], lane, val);
-            publish_task<2>(val, d.partials, t, lane);
+            publish_unit<2>(val, reducer_of(d), ntasks, t, lane);
         }
     } else {
         ntasks = gridDim.x * kWarps;
@@ -862,10 +921,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__
             v[0] += val[0];
             v[1] += val[1];
         });
-        publish_task<2>(v, d.partials, gw, lane);
+        publish_unit<2>(v, reducer_of(d), ntasks, gw, lane);
     }
     double tot[2];
-    if (reduce_tasks<2>(d.partials, ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
+    if (reduce_units<2>(reducer_of(d), ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
         threadIdx.x == 0) {
         const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter);
         if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
@@ -1294,10 +1353,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc
             run_task_b_staged<T, VEC, TY, INIT, D, false>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
         else
             run_task_b_staged<T, VEC, TY, INIT, D, true>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
-        publish_task<2>(val, d.partials, t, lane);
+        publish_unit<2>(val, reducer_of(d), ntasks, t, lane);
     }
     double tot[2];
-    if (reduce_tasks<2>(d.partials, ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
+    if (reduce_units<2>(reducer_of(d), ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
         threadIdx.x == 0) {
         const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter);
         if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);

@@ -330,6 +330,33 @@ def test_asynchronized_picard_step_and_option_checks(g, ctx):
         assert ei.value.status == g.GMAF_INVALID_ARG
 
 
+@pytest.mark.parametrize("precision,variant", [(0, 2322), (0, 1002002), (1, 204322), (1, 4082)])
+def test_two_level_reduction_matches_one_level_and_oracle(g, monkeypatch, precision, variant):
+    """The chunked (two-level) reduction of the phase sums, forced on a small problem:
+    same iterate as the one-level sum up to rounding, and the oracle's solution."""
+    nth, nz, K = 132, 45, 9
+    conds = states(K, seed=41)
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
+    args = [dev(D), dev(aE), dev(aN), dev(S)]
+    n = K * nth * nz
+    monkeypatch.setenv("GMAF_VARIANT", str(variant))
+    out = {}
+    for chunked in ("1", "1000000000"):
+        monkeypatch.setenv("GMAF_CHUNKED_FROM", chunked)
+        c = g.Context()
+        p = zeros(n)
+        st, it, rel = g.gmaf_solve_joint(c.handle, nth, nz, K, *args, p,
+                                         g.solver_opts(eps=1e-10, precision=precision))
+        c.close()
+        assert st == 0 and rel <= 1e-9
+        out[chunked] = (host(p), it)
+    (p2, i2), (p1, i1) = out["1"], out["1000000000"]
+    assert abs(i2 - i1) <= 1
+    assert rel_l2(p2, p1) <= (1e-9 if precision == 0 else 1e-6)
+    sto, po, ito, _, _ = oracle.solve_joint(nth, nz, D, aE, aN, S, precond=1, omega=1.2, eps=1e-10)
+    assert rel_l2(p2.reshape(K, nz, nth), po) <= (1e-9 if precision == 0 else 1e-6)
+
+
 def test_hbm_budget_is_enforced(g):
     c = g.Context(hbm_budget_bytes=1 << 20)
     n = 9 * 256 * 128
