@@ -702,6 +702,15 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
     hm.groups = d_groups;
     hm.msc = msc;
     hm.partials = partials;
+    // two-level reduction per condition: chunks of kChunk tasks; the counters
+    // ([kMaxGroups] group counters, then the chunk counters) are zero between launches
+    const long long nch = (ntiles + kChunk - 1) / kChunk;
+    for (int k = 0; k <= K; ++k) hm.chunk_off[k] = (unsigned)(nch * k);
+    GMAF_TRY(ensure(ctx, B_CHUNK, (size_t)2 * nch * K * sizeof(double)));
+    GMAF_TRY(ensure(ctx, B_CHUNKCTR, (size_t)(kMaxGroups + nch * K) * sizeof(unsigned)));
+    hm.chunk_sum = (double *)ctx->buf[B_CHUNK];
+    hm.group_ctr = (unsigned *)ctx->buf[B_CHUNKCTR];
+    hm.chunk_ctr = hm.group_ctr + kMaxGroups;
     const int zero = 0;
     // pageable sources: each copy has consumed its source when it returns
     GMAF_CUDA(cudaMemcpyAsync(d_slot0, &zero, sizeof(int), cudaMemcpyHostToDevice, s));

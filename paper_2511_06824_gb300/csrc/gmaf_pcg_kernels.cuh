@@ -1369,9 +1369,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc
 // scalars, synchronized criterion and buffers) in one persistent launch per CG
 // phase.  Global task t belongs to group g with task_off[g] <= t < task_off[g+1].
 // Groups whose run is done are skipped (a device-side active mask).  Each task
-// publishes its sums at its global index and the last block reduces every
-// group over its own task range in task order, with the same order as a
-// single-group run, so a group's iterates do not depend on the other groups.
+// publishes its sums at its global index.  The sums of a group are reduced in
+// two levels relative to the group (chunks of kChunk of its tasks, then its
+// chunks), in a fixed order, so a group's iterates do not depend on the other
+// groups; the warp that completes a group applies the group's scalar update at
+// once, so groups finish in parallel, and the last block only tells whether
+// any group is still active.
 
 constexpr int kMaxGroups = 64;
 
@@ -1383,7 +1386,55 @@ struct MultiDesc {
     const PcgDesc<T> *groups;      // device array [ngroups]
     Scalars *msc;                  // tickets and task counters of the batched launches
     double *partials;              // [total_tasks][2]
+    unsigned chunk_off[kMaxGroups + 1];   // first chunk of each group (kChunk tasks a chunk)
+    double *chunk_sum;             // [chunks][2]
+    unsigned *chunk_ctr;           // [chunks], zero between launches
+    unsigned *group_ctr;           // [ngroups], zero between launches
 };
+
+// Task t of group g has published its NV sums at partials[t].  Counts it in its
+// chunk; the warp completing the chunk stores the chunk sum (the chunk's tasks
+// in order) and counts the chunk in the group; the warp completing the group
+// gets the group's totals (its chunk sums in order) and returns true.
+template <int NV, typename T>
+__device__ __forceinline__ bool group_complete(const MultiDesc<T> &m, int g, unsigned t, int lane,
+                                               double (&tot)[NV])
+{
+    const unsigned off = m.task_off[g], tl = t - off, ntl = m.task_off[g + 1] - off;
+    const unsigned cl = tl / kChunk, c = m.chunk_off[g] + cl;
+    const unsigned cnt = min((unsigned)kChunk, ntl - cl * kChunk);
+    unsigned prev = 0;
+    if (lane == 0) {
+        __threadfence();
+        prev = atomicAdd(&m.chunk_ctr[c], 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != cnt - 1) return false;
+    __threadfence();
+    const unsigned u = off + cl * kChunk + (unsigned)lane;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const double x = warp_sum_d((unsigned)lane < cnt ? __ldcg(&m.partials[(size_t)u * NV + q]) : 0.0);
+        if (lane == 0) m.chunk_sum[(size_t)c * 2 + q] = x;
+    }
+    const unsigned c0 = m.chunk_off[g], nch = m.chunk_off[g + 1] - c0;
+    if (lane == 0) {
+        m.chunk_ctr[c] = 0u;
+        __threadfence();
+        prev = atomicAdd(&m.group_ctr[g], 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != nch - 1) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double a = 0.0;
+        for (unsigned i = (unsigned)lane; i < nch; i += 32) a += __ldcg(&m.chunk_sum[(size_t)(c0 + i) * 2 + q]);
+        tot[q] = warp_sum_d(a);
+    }
+    if (lane == 0) m.group_ctr[g] = 0u;
+    return true;
+}
 
 __device__ __forceinline__ int group_of(const unsigned *off, int ng, unsigned t)
 {
@@ -1393,33 +1444,6 @@ __device__ __forceinline__ int group_of(const unsigned *off, int ng, unsigned t)
         if (off[mid] <= t) lo = mid; else hi = mid - 1;
     }
     return lo;
-}
-
-// Block-wide sum of NV task sums over tasks [lo, hi) in task order (last block).
-template <int NV>
-__device__ __forceinline__ void reduce_range(const double *partials, unsigned lo, unsigned hi,
-                                             double (&tot)[NV])
-{
-    __shared__ double red[NV][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double s = 0.0;
-        for (unsigned t = lo + threadIdx.x; t < hi; t += blockDim.x)
-            s += __ldcg(&partials[(size_t)t * NV + q]);
-        s = warp_sum_d(s);
-        if (lane == 0) red[q][wid] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double t = 0.0;
-            for (int w = 0; w < nw; ++w) t += red[q][w];
-            tot[q] = t;
-        }
-    }
-    __syncthreads();
 }
 
 __device__ __forceinline__ bool last_block(unsigned *ticket)
@@ -1473,19 +1497,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
                                                k, first != 0, (T)alpha, (T)beta,
                                             su[wp], sa[wp], lane);
         publish_task<1>(val, m.partials, t, lane);
+        double tot[1];
+        if (group_complete<1>(m, g, t, lane, tot) && lane == 0 && !done) {   // active all launch
+            d.sc->guard += 1;
+            finish_a(d.sc, tot[0]);
+        }
     }
     if (!last_block(&m.msc->ticket[kTicketA])) return;
-    for (int g = 0; g < m.ngroups; ++g) {
-        Scalars *sc = m.groups[g].sc;
-        const int active = !sc->done;          // unchanged since the launch began
-        double tot[1];
-        reduce_range<1>(m.partials, m.task_off[g], m.task_off[g + 1], tot);
-        if (threadIdx.x == 0 && active) {
-            sc->guard += 1;
-            finish_a(sc, tot[0]);
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
         m.msc->ticket[kTicketA] = 0u;
         m.msc->task_ctr[0] = 0u;
@@ -1527,21 +1545,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
                                       (T)alpha, sy[wp], sw[wp], sa[wp],
                                           lane, val);
         publish_task<2>(val, m.partials, t, lane);
+        double tot[2];
+        if (group_complete<2>(m, g, t, lane, tot) && lane == 0 && !done)   // active all launch
+            finish_b<false>(d.sc, tot[0], tot[1], k, d.eps, d.max_iter);
     }
     if (!last_block(&m.msc->ticket[kTicketB])) return;
-    int any = 0;
-    for (int g = 0; g < m.ngroups; ++g) {
-        const PcgDesc<T> &d = m.groups[g];
-        Scalars *sc = d.sc;
-        const int active = !sc->done;
-        double tot[2];
-        reduce_range<2>(m.partials, m.task_off[g], m.task_off[g + 1], tot);
-        if (threadIdx.x == 0 && active) {
-            const int done = finish_b<false>(sc, tot[0], tot[1], sc->iter, d.eps, d.max_iter);
-            any |= !done;
-        }
-        __syncthreads();
-    }
+    // every group has been completed (and updated) by now
+    int active = 0;
+    for (int g = threadIdx.x; g < m.ngroups; g += blockDim.x) active |= !m.groups[g].sc->done;
+    const int any = __syncthreads_or(active);
     if (threadIdx.x == 0) {
         m.msc->done = !any;                   // no group active any more
         m.msc->ticket[kTicketB] = 0u;

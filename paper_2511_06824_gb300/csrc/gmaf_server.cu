@@ -164,6 +164,10 @@ struct gmaf_server {
     Scalars *msc;
     double *mpart;
     size_t mpart_cap;
+    double *mchunk;                // chunk sums of the batched reduction
+    size_t mchunk_cap;
+    unsigned *mctr;                // [kMaxGroups] group counters, then the chunk counters
+    size_t mctr_cap;
     bool dirty;
     MultiDesc<float> hm;
     int grid_m;
@@ -371,6 +375,27 @@ static int retire(gmaf_server *sv, Request *r, int status, double true_rel)
 }
 
 // Rebuild the batched-launch table after the active set or a descriptor changed.
+// Grow a device buffer to at least `need` bytes, zero-filled when (re)allocated;
+// the stream is synchronised before the old buffer is freed.
+static int grow_zeroed(gmaf_server *sv, void **buf, size_t *cap, size_t need)
+{
+    if (need <= *cap) return GMAF_OK;
+    cudaError_t e = cudaStreamSynchronize(sv->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return GMAF_OUT_OF_MEMORY;
+    }
+    e = cudaMemsetAsync(*buf, 0, need, sv->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    *cap = need;
+    return GMAF_OK;
+}
+
 static int rebuild_table(gmaf_server *sv)
 {
     MultiDesc<float> &hm = sv->hm;
@@ -400,6 +425,21 @@ static int rebuild_table(gmaf_server *sv)
         sv->mpart_cap = need;
     }
     hm.partials = sv->mpart;
+    // two-level reduction: chunks of kChunk tasks, counted per group
+    unsigned cacc = 0;
+    for (size_t g = 0; g < sv->active.size(); ++g) {
+        hm.chunk_off[g] = cacc;
+        cacc += (unsigned)((sv->active[g]->ntasks + kChunk - 1) / kChunk);
+    }
+    hm.chunk_off[hm.ngroups] = cacc;
+    int gst = grow_zeroed(sv, (void **)&sv->mchunk, &sv->mchunk_cap,
+                          (size_t)2 * (cacc ? cacc : 1) * sizeof(double));
+    if (gst == GMAF_OK)
+        gst = grow_zeroed(sv, (void **)&sv->mctr, &sv->mctr_cap, (size_t)(kMaxGroups + cacc) * sizeof(unsigned));
+    if (gst != GMAF_OK) return gst;
+    hm.chunk_sum = sv->mchunk;
+    hm.group_ctr = sv->mctr;
+    hm.chunk_ctr = sv->mctr + kMaxGroups;
     cudaError_t e = cudaSuccess;
     if (!groups.empty())
         e = cudaMemcpyAsync(sv->d_groups, groups.data(), groups.size() * sizeof(PcgDesc<float>),
@@ -521,6 +561,10 @@ int gmaf_server_create(gmaf_ctx *ctx, size_t hbm_budget_bytes, gmaf_server **out
     sv->msc = nullptr;
     sv->mpart = nullptr;
     sv->mpart_cap = 0;
+    sv->mchunk = nullptr;
+    sv->mchunk_cap = 0;
+    sv->mctr = nullptr;
+    sv->mctr_cap = 0;
     sv->dirty = true;
     sv->hm = MultiDesc<float>{};
     sv->grid_m = 1;
@@ -554,6 +598,8 @@ int gmaf_server_destroy(gmaf_server *sv)
     cudaFree(sv->d_groups);
     cudaFree(sv->msc);
     if (sv->mpart) cudaFree(sv->mpart);
+    if (sv->mchunk) cudaFree(sv->mchunk);
+    if (sv->mctr) cudaFree(sv->mctr);
     delete sv;
     return e == cudaSuccess ? GMAF_OK : GMAF_CUDA_ERROR;
 }
