@@ -31,6 +31,7 @@
 
 #include "gmaf_internal.cuh"
 #include "gmaf_pcg_kernels.cuh"
+#include "gmaf_mphase_kernels.cuh"
 
 namespace gmaf {
 

@@ -21,6 +21,7 @@
 
 #include "gmaf_internal.cuh"
 #include "gmaf_pcg_kernels.cuh"
+#include "gmaf_mphase_kernels.cuh"
 
 namespace gmaf {
 
