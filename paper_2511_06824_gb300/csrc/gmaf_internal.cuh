@@ -59,7 +59,7 @@ struct PcgDesc {
     const T *b;                    // right-hand side, [K][n]
     T *p, *z, *v;
     T *u[2], *r[2];
-    T omega, c1;                   // c1 = omega (2 - omega)
+    T omega;                       // ASSOR relaxation factor
     double eps;
     int max_iter;
     cudaGraphConditionalHandle cond;

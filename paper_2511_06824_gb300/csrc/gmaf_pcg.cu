@@ -676,7 +676,6 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
         h.r[0] = r0 + o;
         h.r[1] = r1 + o;
         h.omega = opts->omega;
-        h.c1 = opts->omega * (2.0 - opts->omega);
         h.eps = opts->eps;
         h.max_iter = opts->max_iter;
         h.sc = gsc + k;
@@ -880,7 +879,6 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         h.r[0] = (double *)ctx->buf[B_R0];
         h.r[1] = (double *)ctx->buf[B_R1];
         h.omega = opts->omega;
-        h.c1 = opts->omega * (2.0 - opts->omega);
         h.eps = opts->eps;
         h.max_iter = opts->max_iter;
         h.sc = dsc;
@@ -978,7 +976,6 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     h.r[0] = (float *)ctx->buf[B_R032];
     h.r[1] = (float *)ctx->buf[B_R132];
     h.omega = (float)opts->omega;
-    h.c1 = (float)(opts->omega * (2.0 - opts->omega));
     h.sc = dsc;
     // The first outer residual and the inner right-hand side are formed before the
     // kernel set is chosen, so that the autotuner times iterations on real data.
@@ -1162,7 +1159,6 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     h.z = vecs[4];
     h.v = vecs[5];
     h.omega = opts->omega;
-    h.c1 = opts->omega * (2.0 - opts->omega);
     h.eps = opts->eps;
     h.max_iter = opts->max_iter;
     h.sc = dsc;

@@ -663,7 +663,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
     constexpr bool BF = sizeof(T) == 4;
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
-    const T omega = d.omega, c1 = d.c1;
+    const T omega = d.omega;
     const bool assor = (d.precond == 1);
     const T *ro_base = d.r[k & 1];
     T *rn_base = d.r[(k + 1) & 1];
@@ -718,9 +718,9 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
             }
         };
 
-        T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
+        T y_m1[VEC], w_m1[VEC], od_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
+        for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = od_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
         T hy_m1 = T(0), hn_m1 = T(0), he_m1 = T(0);
         RowB<T, VEC> nx;
         load_row(tk.j0 - 1, nx);
@@ -748,10 +748,10 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
             if (BF) aw_wrap = __shfl_sync(0xffffffffu, he_m1, 1);
             __syncwarp();
             // first ASSOR pass on row jr: w = y + omega D^-1 (lower couplings) y
-            T w[VEC];
+            T w[VEC], od[VEC];                 // od = omega D^-1, reused by the second pass
             T hw = T(0);
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) w[q] = T(0);
+            for (int q = 0; q < VEC; ++q) w[q] = od[q] = T(0);
             if (assor && inrow && jr >= tk.j0) {
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
@@ -761,7 +761,8 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
                     if (gi > 0)                                                        // west
                         sum += ((q > 0) ? cur.e[q - 1] : ab[s - 1]) * ((q > 0) ? y[q - 1] : yb[s - 1]);
                     if (gi == nth - 1) sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);  // east, wrapped
-                    w[q] = y[q] + omega * cur.dI[q] * sum;
+                    od[q] = omega * cur.dI[q];
+                    w[q] = y[q] + od[q] * sum;
                 }
                 // halo w (used for lanes 1, 2; in FP32 the others compute and discard it)
                 if (BF || lane == 1 || lane == 2) {
@@ -772,7 +773,11 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
                     hw = hy + omega * cur.hd * sum;
                 }
             }
-            // second pass on row jo = jr - 1: z = c1 (w + omega D^-1 (upper couplings) w)
+            // second pass on row jo = jr - 1: z = w + omega D^-1 (upper couplings) w.
+            // The constant factor c1 = omega (2 - omega) of Eq. 3.6 is left out: PCG is
+            // invariant under scaling the preconditioner by a positive constant (alpha
+            // takes the inverse factor; p and r are unchanged), and it saves an FP64
+            // multiply per cell where FP64 arithmetic bounds the phase
             const int jo = jr - 1;
             if (jo >= tk.j0 && jo < tk.jend) {
                 T zz[VEC];
@@ -787,7 +792,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
                         if (gi == 0)                                                                     // west, wrapped
                             sum += (BF ? aw_wrap : __ldg(aE + (size_t)jo * nth + nth - 1)) *
                                    ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
-                        zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
+                        zz[q] = w_m1[q] + od_m1[q] * sum;      // Eq. 3.6 without its factor c1
                     } else {
                         zz[q] = y_m1[q];
                     }
@@ -812,7 +817,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
             for (int q = 0; q < VEC; ++q) {
                 y_m1[q] = y[q];
                 w_m1[q] = w[q];
-                d_m1[q] = cur.dI[q];
+                od_m1[q] = od[q];
                 n_m1[q] = cur.n[q];
                 e_m1[q] = cur.e[q];
                 r_m1[q] = r1[q];
@@ -1154,7 +1159,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     static_assert(VEC % CH == 0, "whole 16-byte chunks per lane");
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
-    const T omega = d.omega, c1 = d.c1;
+    const T omega = d.omega;
     const bool assor = (d.precond == 1);
     RowAcc<T> arz, arr;
     const size_t off = (size_t)tk.cond * (size_t)n;
@@ -1197,9 +1202,9 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         cp_commit();
     };
 
-    T y_m1[VEC], w_m1[VEC], d_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
+    T y_m1[VEC], w_m1[VEC], od_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = d_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
+    for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = od_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
     T hy_m1 = T(0), hn_m1 = T(0), he_m1 = T(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
@@ -1241,10 +1246,10 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         T aw_wrap = T(0);
         if (BF) aw_wrap = __shfl_sync(0xffffffffu, he_m1, 1);
         __syncwarp();
-        T w[VEC];
+        T w[VEC], od[VEC];                       // od = omega D^-1, reused by the second pass
         T hw = T(0);
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) w[q] = T(0);
+        for (int q = 0; q < VEC; ++q) w[q] = od[q] = T(0);
         if (assor && inrow && jr >= tk.j0) {
             const T *ab = cur + 3 * NB;          // aE of row jr with its halo
             const bool south = jr > 0;
@@ -1256,7 +1261,8 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
                 const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
                 if (!EDGE || gi > 0) sum += aW * yW;
                 if (EDGE && gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
-                w[q] = y[q] + omega * dI[q] * sum;
+                od[q] = omega * dI[q];
+                w[q] = y[q] + od[q] * sum;
             }
             if (BF || lane == 1 || lane == 2) {
                 T sum = south ? hn_m1 * hy_m1 : T(0);
@@ -1280,7 +1286,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
                     if (EDGE && gi == 0)
                         sum += (BF ? aw_wrap : __ldg(aE + (size_t)jo * nth + nth - 1)) *
                                ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
-                    zz[q] = c1 * (w_m1[q] + omega * d_m1[q] * sum);
+                    zz[q] = w_m1[q] + od_m1[q] * sum;   // Eq. 3.6 without its factor c1
                 } else {
                     zz[q] = y_m1[q];
                 }
@@ -1306,7 +1312,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         for (int q = 0; q < VEC; ++q) {
             y_m1[q] = y[q];
             w_m1[q] = w[q];
-            d_m1[q] = dI[q];
+            od_m1[q] = od[q];
             n_m1[q] = nv[q];
             e_m1[q] = ev[q];
             r_m1[q] = r1[q];

@@ -296,7 +296,6 @@ static int admit(gmaf_server *sv, Request *r)
     h.r[0] = r->r32[0];
     h.r[1] = r->r32[1];
     h.omega = (float)r->in.omega;
-    h.c1 = (float)(r->in.omega * (2.0 - r->in.omega));
     h.sc = r->sc_in;
     h.partials = r->part;
     // FP64 residual descriptor
