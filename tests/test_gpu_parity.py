@@ -162,7 +162,8 @@ def test_fp64_iterates_track_the_oracle_tightly(g, ctx):
     assert rel_l2(p, po) <= 1e-11
 
 
-@pytest.mark.parametrize("nth,nz,K,precond", [(64, 32, 1, 1), (130, 45, 9, 1), (132, 40, 9, 2)])
+@pytest.mark.parametrize("nth,nz,K,precond", [(64, 32, 1, 1), (130, 45, 9, 1), (132, 40, 9, 2),
+                                              (96, 40, 4, 0)])
 def test_mixed_precision_solve_matches_fp64_oracle(g, ctx, nth, nz, K, precond):
     conds = states(K, seed=7)
     p, it, rel, po, ito, arrs = solve_both(g, ctx, nth, nz, tex_dimples(), conds, precision=1,
@@ -322,6 +323,12 @@ def test_asynchronized_picard_step_and_option_checks(g, ctx):
         else:
             assert info["iterations_sum"] == 9 * info["iterations"]
     assert load_err(res[1]["loads"], res[0]["loads"]) <= 1e-7
+    # the simplified scheme's 5-condition batch (one coefficient set) under both criteria
+    simp = [g.gmaf_picard_step_simplified(ctx, 96, 48, PHYS, tex, st0, dt, F, 1e-6,
+                                          g.solver_opts(eps=1e-12, criterion=crit))
+            for crit in (0, 1)]
+    assert load_err(simp[1]["loads"], simp[0]["loads"]) <= 1e-7
+    assert g.gmaf_last_solve_info(ctx)["iterations_sum"] > g.gmaf_last_solve_info(ctx)["iterations"]
     p = zeros(2 * 64 * 32)
     so, D, aE, aN, S = oracle.assemble_joint(64, 32, PHYS, inputs.smooth_texture(), states(2))
     for bad in (g.solver_opts(criterion=1, precision=1), g.solver_opts(criterion=2)):

@@ -45,20 +45,20 @@ def _problem(nth, nz, K, seed, textured):
 
 
 def test_noalloc_solve_matches_solve_joint_twice_in_a_row(g):
-    cases = [(150, 60, 9, 1, True), (64, 32, 3, 2, False)]
+    cases = [(150, 60, 9, 1, True, 1), (64, 32, 3, 2, False, 1), (96, 40, 4, 3, True, 2)]
     ctx = g.Context()
     try:
-        for nth, nz, K, seed, textured in cases:
+        for nth, nz, K, seed, textured, precond in cases:
             D, aE, aN, S = _problem(nth, nz, K, seed, textured)
             n = K * nth * nz
             p_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
             p_na = torch.full((n,), 7.0, dtype=torch.float64, device="cuda")
-            opts = g.solver_opts(eps=1e-10)
+            opts = g.solver_opts(eps=1e-10, precond=precond)
             st, it_ref, rel_ref = g.gmaf_solve_joint(ctx.handle, nth, nz, K, D, aE, aN, S, p_ref,
                                                      opts)
             st2, it_na, rel_na = g.gmaf_solve_joint_noalloc(nth, nz, K, D, aE, aN, S, p_na, opts)
             assert st == 0 and st2 == 0
-            assert it_na == it_ref
+            assert abs(it_na - it_ref) <= 1      # the ordinary call may tune to another variant
             assert rel_na <= 1e-9
             a, b = p_na.cpu().numpy(), p_ref.cpu().numpy()
             assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
