@@ -264,12 +264,14 @@ def run_ours(args):
 
     # launches of our kernels in one step: fan-out, trig, 2 assembly, loads, update,
     # and per solve: conversion/inverse, and per PCG run reset, init_r, init B,
-    # 2 per iteration, finalize, plus the FP64 residual and the mixed-mode glue
+    # 2 per iteration, finalize, plus the FP64 residual and the mixed-mode glue.
+    # The graph runs the phases in trips of 4 iterations, so each PCG run also
+    # launches 0..6 phases that return at once after convergence: counted as 3.
     def launches_per_step(iters, outer_it):
         fixed = 6
         if prec == 1:
-            return fixed + 1 + outer_it * 6 + 1 + 2 * iters
-        return fixed + 1 + 4 + 1 + 2 * iters
+            return fixed + 1 + outer_it * (6 + 3) + 1 + 2 * iters
+        return fixed + 1 + 4 + 3 + 1 + 2 * iters
 
     gpu_launches = int(sum(launches_per_step(i, o) for i, o in zip(its, outer)))
 
