@@ -75,6 +75,7 @@ struct KernelSet {
     int W, TY, id;
     size_t smem_b;             // dynamic shared memory of the phase-B kernels
     int sched;
+    size_t smem_a;             // dynamic shared memory of the phase-A kernel
 };
 
 // id = 1000 VEC + 10 TY + MINB (dynamic), 1000000 + 1000 VEC + MINB (static).
@@ -105,7 +106,26 @@ static KernelSet<T> ks_staged()
             100000 * D + 1000 * VEC + 10 * TY + MINB, smem, 0};
 }
 
-constexpr int kMaxVariants = 14;
+// Both phases staged D rows ahead; id + 300000 D.
+template <typename T, int VEC, int TY, int MINB, int D>
+static KernelSet<T> ks_staged_ab()
+{
+    KernelSet<T> ks = ks_staged<T, VEC, TY, MINB, D>();
+    const size_t smem = (size_t)kWarps * RingA<T, VEC>::per_warp(D) * sizeof(T);
+    const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, D>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaGetLastError();
+        attr = true;
+    }
+    ks.a = a;
+    ks.smem_a = smem;
+    ks.id += 200000 * D;
+    return ks;
+}
+
+constexpr int kMaxVariants = 16;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
 static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
@@ -115,6 +135,8 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
         // 32-row tasks suit the largest grids; 16 and 8 rows and the static
         // schedule keep every warp busy on smaller ones (1024 x 512 x 9 has only
         // 1152 tasks of 32 rows for 2432 resident warps)
+        out[n++] = ks_staged_ab<float, 4, 32, 2, 2>();
+        out[n++] = ks_staged_ab<float, 4, 16, 2, 2>();
         out[n++] = ks_of<float, 4, 32, 2>(0);
         out[n++] = ks_staged<float, 4, 32, 2, 2>();
         out[n++] = ks_staged<float, 4, 16, 2, 2>();
@@ -237,7 +259,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
         for (int q = 0; q < pairs && e == cudaSuccess; ++q) {
             kp.func = (void *)run.ks.a;
             kp.gridDim = dim3(run.grid_a);
-            kp.sharedMemBytes = 0;
+            kp.sharedMemBytes = (unsigned)run.ks.smem_a;
             e = cudaGraphAddKernelNode(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
             if (e == cudaSuccess) {
                 kp.func = (void *)run.ks.b;
@@ -292,7 +314,8 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
         // static schedule: both phases get the same warps, so that phase A walks
         // exactly phase B's ranges backward; groups of >= 4 rows on average
         int occ_a = 0, occ_b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, ks.a, kThreads, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, ks.a, kThreads, ks.smem_a) !=
+            cudaSuccess)
             occ_a = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, ks.b, kThreads, ks.smem_b) !=
             cudaSuccess)
@@ -305,7 +328,7 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
         h.sgroups = G;
         run.grid_a = run.grid_b = (int)((warps + kWarps - 1) / kWarps);
     } else {
-        run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms);
+        run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms, ks.smem_a);
         run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b);
     }
     run.grid_s = stream_grid(h.n * h.K, ctx->num_sms);
@@ -376,7 +399,7 @@ static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand
             const int warm = 3, reps = 10;
             for (int q = 0; q < warm + reps; ++q) {
                 if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
-                GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s));
+                GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s, tr.ks.smem_a));
                 GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s, tr.ks.smem_b));
             }
             GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
@@ -523,7 +546,7 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
         if (*done_h) break;
         for (int q = 0; q < chunk; ++q) {
             clk.begin(s);
-            GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s));
+            GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s, run.ks.smem_a));
             clk.end(s, 0);
             clk.begin(s);
             GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s, run.ks.smem_b));
@@ -1167,7 +1190,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
     h.tiles_x = (nth + ks.W - 1) / ks.W;
     h.tiles_y = (nz + ks.TY - 1) / ks.TY;
     h.ntiles = (long long)h.tiles_x * h.tiles_y * K;
-    const int grid_a = phase_grid(ks.a, h.ntiles, num_sms);
+    const int grid_a = phase_grid(ks.a, h.ntiles, num_sms, ks.smem_a);
     const int grid_b = phase_grid(ks.b, h.ntiles, num_sms, ks.smem_b);
     const int grid_s = stream_grid(N, num_sms);
     long long np = 2 * h.ntiles;
@@ -1221,7 +1244,7 @@ extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, c
             if (e != cudaSuccess) return cuda_status(e);
             if (done) break;
             for (int q = 0; q < chunk && e == cudaSuccess; ++q) {
-                e = launch<double>(ks.a, grid_a, d_desc, s);
+                e = launch<double>(ks.a, grid_a, d_desc, s, ks.smem_a);
                 if (e == cudaSuccess) e = launch<double>(ks.b, grid_b, d_desc, s, ks.smem_b);
             }
             if (e != cudaSuccess) return cuda_status(e);

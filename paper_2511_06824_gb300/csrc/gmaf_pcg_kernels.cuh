@@ -1133,6 +1133,202 @@ __device__ __forceinline__ void cp_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------------------------------ phase A, staged rows
+//
+// Same arithmetic and order as run_task_a (forward marching), but the six input
+// rows (z, u', D, aE, aN, p) and the halo columns (z, u' of lanes 0 and 1, aE of
+// lane 0) are staged by cp.async into a per-warp ring of D + 1 rows, D rows
+// ahead.  A row's values move to registers (and the aE and u rows to their own
+// shared rows) when it is consumed, so the slot that the next copy overwrites is
+// never read again.
+
+template <typename T, int VEC>
+struct RingA {
+    static constexpr int W = 32 * VEC, NB = W + 8, NF = 6;
+    // elements per warp: (D+1) staged rows of NF fields, plus the u and aE rows
+    __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
+};
+
+template <typename T, int VEC, int TY, int D>
+__device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const Task &tk, int k,
+                                                    bool first, T alpha_prev, T beta, T *ring,
+                                                    T *ub, T *ab, int lane)
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8, NF = 6, SLOT = NF * NB;
+    constexpr int CH = 16 / (int)sizeof(T);
+    static_assert(VEC % CH == 0, "whole 16-byte chunks per lane");
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n;
+    RowAcc<T> acc;
+    const size_t off = (size_t)tk.cond * (size_t)n;
+    const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
+    const T *uo_base = d.u[(k + 1) & 1];
+    T *un = d.u[k & 1] + off;
+    T *vv = d.v + off;
+    T *pp = d.p + off;
+    const int c0 = tk.i0 + lane * VEC;
+    const bool owned = c0 < nth;
+    const int g0 = wrap_col(c0, nth);
+    const int sown = 4 + lane * VEC;
+    // halo: lane 0 -> column i0 - 1 (slot 3), lane 1 -> column i0 + W (slot W + 4);
+    // the other lanes read lane 1's slot and write the spare slot W + 7
+    const int hg = wrap_col(lane == 0 ? tk.i0 - 1 : tk.i0 + W, nth);
+    const int hs = lane == 0 ? 3 : W + 4;
+    const int hslot_u = lane < 2 ? hs : W + 7;
+    const int hslot_a = lane == 0 ? hs : W + 7;
+    // fields: 0 z, 1 u', 2 D, 3 aE, 4 aN, 5 p
+    const T *src[NF] = {d.z + off, uo_base + off, d.D + coff, d.aE + coff, d.aN + coff, pp};
+
+    auto issue = [&](int jr) {
+        if (jr >= 0 && jr < nz && jr >= tk.j0 - 1 && jr <= tk.jend) {
+            T *slot = ring + ((jr + 1) % (D + 1)) * SLOT;
+            const size_t rq = (size_t)jr * nth;
+            const bool in = jr >= tk.j0 && jr < tk.jend;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (first && (f == 1 || f == 5)) continue;     // no u', no p update
+                if (!in && (f == 2 || f == 3 || f == 5)) continue;
+                if (!owned && f == 5) continue;
+#pragma unroll
+                for (int c = 0; c < VEC; c += CH) cp_async16(slot + f * NB + sown + c, src[f] + rq + g0 + c);
+            }
+            if (lane < 2) {
+                cp_async_small<sizeof(T)>(slot + hs, src[0] + rq + hg);
+                if (!first) cp_async_small<sizeof(T)>(slot + NB + hs, src[1] + rq + hg);
+                if (lane == 0) cp_async_small<sizeof(T)>(slot + 3 * NB + hs, src[3] + rq + hg);
+            }
+        }
+        cp_commit();
+    };
+
+    T u_m1[VEC], u_m2[VEC], uo_m1[VEC], D_m1[VEC], e_m1[VEC], n_m1[VEC], n_m2[VEC], p_m1[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q)
+        u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = T(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
+    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+        issue(jr + D);
+        cp_wait<D>();
+        __syncwarp();
+        const T *cur = ring + ((jr + 1) % (D + 1)) * SLOT;
+        const bool inrow = jr >= 0 && jr < nz;
+        const bool in = inrow && jr >= tk.j0 && jr < tk.jend;
+        T zv[VEC], uov[VEC], Dv[VEC], ev[VEC], nv[VEC], pv[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) zv[q] = uov[q] = Dv[q] = ev[q] = nv[q] = pv[q] = T(0);
+        T hz = T(0), huo = T(0), he = T(0);
+        if (inrow) {
+            Vec<T, VEC>::ldrw(cur + sown, zv);
+            if (!first) Vec<T, VEC>::ldrw(cur + NB + sown, uov);
+            Vec<T, VEC>::ldrw(cur + 4 * NB + sown, nv);
+            if (in) {
+                Vec<T, VEC>::ldrw(cur + 2 * NB + sown, Dv);
+                Vec<T, VEC>::ldrw(cur + 3 * NB + sown, ev);
+                if (!first) Vec<T, VEC>::ldrw(cur + 5 * NB + sown, pv);
+            }
+            hz = cur[hs];
+            if (!first) huo = cur[NB + hs];
+            he = cur[3 * NB + hs];
+        }
+        T u[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) u[q] = first ? zv[q] : zv[q] + beta * uov[q];
+        const T hu = first ? hz : hz + beta * huo;
+        const int jo = jr - 1;
+        if (jo >= tk.j0 && jo < tk.jend) {
+            T vout[VEC];
+            T rowsum = T(0);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const int s = sown + q;
+                const T uE = (q < VEC - 1) ? u_m1[q + 1] : ub[s + 1];
+                const T uW = (q > 0) ? u_m1[q - 1] : ub[s - 1];
+                const T aW = (q > 0) ? e_m1[q - 1] : ab[s - 1];
+                vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
+                          n_m2[q] * u_m2[q];
+                rowsum += u_m1[q] * vout[q];
+            }
+            if (owned) {
+                const size_t qo = (size_t)jo * nth + g0;
+                Vec<T, VEC>::st(un + qo, u_m1);
+                Vec<T, VEC>::st(vv + qo, vout);
+                if (!first) {
+                    T pn[VEC];
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) pn[q] = p_m1[q] + alpha_prev * uo_m1[q];
+                    Vec<T, VEC>::st(pp + qo, pn);
+                }
+                acc.add_row(rowsum);
+            }
+        }
+        __syncwarp();
+        Vec<T, VEC>::st(ub + sown, u);
+        Vec<T, VEC>::st(ab + sown, ev);
+        ub[hslot_u] = hu;
+        ab[hslot_a] = he;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            u_m2[q] = u_m1[q];
+            u_m1[q] = u[q];
+            uo_m1[q] = uov[q];
+            n_m2[q] = n_m1[q];
+            n_m1[q] = nv[q];
+            D_m1[q] = Dv[q];
+            e_m1[q] = ev[q];
+            p_m1[q] = pv[q];
+        }
+    }
+    cp_wait<0>();
+    __syncwarp();
+    return acc.value();
+}
+
+template <typename T, int VEC, int TY, int MINB, int D>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_a_staged(const PcgDesc<T> *__restrict__ dp)
+{
+    using R = RingA<T, VEC>;
+    constexpr int W = 32 * VEC;
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    extern __shared__ __align__(16) unsigned char g_dyn_smem_a[];
+    __shared__ int s_done, s_k, s_first;
+    __shared__ double s_alpha, s_beta;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_k = sc->iter;
+        s_first = sc->first;
+        s_alpha = sc->alpha;
+        s_beta = sc->beta;
+        if (blockIdx.x == 0) {
+            // stop unless phase B's last block asks for another iteration
+            if (d.use_cond) cudaGraphSetConditional(d.cond, 0u);
+            sc->guard += 1;
+        }
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *mine = reinterpret_cast<T *>(g_dyn_smem_a) + (size_t)wp * R::per_warp(D);
+    T *ring = mine;
+    T *ub = mine + (D + 1) * R::NF * R::NB;
+    T *ab = ub + R::NB;
+    const unsigned ntasks = (unsigned)d.ntiles;
+    for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
+         t = next_task(&sc->task_ctr[0], lane)) {
+        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+        const double val[1] = {run_task_a_staged<T, VEC, TY, D>(d, tk, s_k, s_first != 0, (T)s_alpha,
+                                                                (T)s_beta, ring, ub, ab, lane)};
+        publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
+    }
+    double tot[1];
+    if (reduce_units<1>(reducer_of(d), ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
+        threadIdx.x == 0)
+        finish_a(sc, tot[0]);
+}
+
 template <typename T, int VEC>
 struct RingB {
     static constexpr int W = 32 * VEC, NB = W + 8, NF = 5;

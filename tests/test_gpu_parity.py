@@ -230,12 +230,14 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
     assert np.array_equal(host(p), outs[0])
 
 
-# dynamic tasks (ids 1000 VEC + 10 TY + MINB) and the static schedule with phase A
-# marching against phase B (ids 1000000 + 1000 VEC + MINB); float VEC > 1 kernels
-# need n_theta % 4 == 0, double ones an even n_theta
+# dynamic tasks (ids 1000 VEC + 10 TY + MINB), phase B staged D rows ahead
+# (+ 100000 D), both phases staged (+ 300000 D), and the static schedule with
+# phase A marching against phase B (ids 1000000 + 1000 VEC + MINB); float VEC > 1
+# kernels need n_theta % 4 == 0, double ones an even n_theta
 @pytest.mark.parametrize("precision,variant,nth,nz,K", [
     (1, 4322, 132, 45, 9), (1, 1004002, 132, 45, 9), (1, 4082, 260, 33, 4),
-    (1, 204162, 132, 45, 9), (1, 204322, 260, 70, 3),
+    (1, 204162, 132, 45, 9), (1, 204322, 260, 70, 3), (1, 604322, 132, 45, 9),
+    (1, 604322, 260, 70, 3), (1, 604162, 132, 45, 9),
     (1, 1001004, 131, 7, 3), (0, 2322, 130, 45, 9), (0, 1002002, 130, 45, 9),
     (0, 1001003, 131, 7, 3), (0, 1001003, 3, 2, 1),
 ])
@@ -337,7 +339,8 @@ def test_asynchronized_picard_step_and_option_checks(g, ctx):
         assert ei.value.status == g.GMAF_INVALID_ARG
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 2322), (0, 1002002), (1, 204322), (1, 4082)])
+@pytest.mark.parametrize("precision,variant", [(0, 2322), (0, 1002002), (1, 204322), (1, 604322),
+                                               (1, 4082)])
 def test_two_level_reduction_matches_one_level_and_oracle(g, monkeypatch, precision, variant):
     """The chunked (two-level) reduction of the phase sums, forced on a small problem:
     same iterate as the one-level sum up to rounding, and the oracle's solution."""
