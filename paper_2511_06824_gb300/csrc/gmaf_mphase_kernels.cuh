@@ -105,19 +105,31 @@ __device__ __forceinline__ bool last_block(unsigned *ticket)
     return s_last != 0;
 }
 
-template <typename T, int VEC, int TY, int MINB>
+// D > 0: the input rows are staged D rows ahead through a per-warp shared ring
+// (dynamic shared memory of kWarps * RingA<T, VEC>::per_warp(D) elements).
+template <typename T, int VEC, int TY, int MINB, int D>
 __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> *__restrict__ mp)
 {
     constexpr int W = 32 * VEC;
     constexpr int NB = W + 8;
     const MultiDesc<T> &m = *mp;
-    __shared__ __align__(16) T su[kWarps][NB];
-    __shared__ __align__(16) T sa[kWarps][NB];
     __shared__ int s_idle;
     if (threadIdx.x == 0) s_idle = m.msc->done;    // every group finished earlier this round
     __syncthreads();
     if (s_idle) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *ring = nullptr, *ub, *ab;
+    if constexpr (D > 0) {
+        extern __shared__ __align__(16) unsigned char g_dyn_smem_ma[];
+        ring = reinterpret_cast<T *>(g_dyn_smem_ma) + (size_t)wp * RingA<T, VEC>::per_warp(D);
+        ub = ring + (D + 1) * RingA<T, VEC>::NF * NB;
+        ab = ub + NB;
+    } else {
+        __shared__ __align__(16) T su[kWarps][NB];
+        __shared__ __align__(16) T sa[kWarps][NB];
+        ub = su[wp];
+        ab = sa[wp];
+    }
     for (unsigned t = next_task(&m.msc->task_ctr[0], lane); t < m.total_tasks;
          t = next_task(&m.msc->task_ctr[0], lane)) {
         const int g = group_of(m.task_off, m.ngroups, t);
@@ -137,10 +149,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         alpha = __shfl_sync(0xffffffffu, alpha, 0);
         beta = __shfl_sync(0xffffffffu, beta, 0);
         double val[1] = {0.0};
-        if (!done)
-            val[0] = run_task_a<T, VEC, false>(d, task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz),
-                                               k, first != 0, (T)alpha, (T)beta,
-                                            su[wp], sa[wp], lane);
+        if (!done) {
+            const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
+            if constexpr (D > 0)
+                val[0] = run_task_a_staged<T, VEC, TY, D>(d, tk, k, first != 0, (T)alpha, (T)beta, ring,
+                                                          ub, ab, lane);
+            else
+                val[0] = run_task_a<T, VEC, false>(d, tk, k, first != 0, (T)alpha, (T)beta, ub, ab, lane);
+        }
         publish_task<1>(val, m.partials, t, lane);
         double tot[1];
         if (group_complete<1>(m, g, t, lane, tot) && lane == 0 && !done) {   // active all launch
@@ -155,20 +171,33 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
     }
 }
 
-template <typename T, int VEC, int TY, int MINB>
+// D > 0: staged D rows ahead (dynamic shared memory of kWarps *
+// RingB<T, VEC>::per_warp(D) elements).
+template <typename T, int VEC, int TY, int MINB, int D>
 __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> *__restrict__ mp)
 {
     constexpr int W = 32 * VEC;
     constexpr int NB = W + 8;
     const MultiDesc<T> &m = *mp;
-    __shared__ __align__(16) T sy[kWarps][NB];
-    __shared__ __align__(16) T sw[kWarps][NB];
-    __shared__ __align__(16) T sa[kWarps][NB];
     __shared__ int s_idle;
     if (threadIdx.x == 0) s_idle = m.msc->done;
     __syncthreads();
     if (s_idle) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *ring = nullptr, *yb, *wb, *ab = nullptr;
+    if constexpr (D > 0) {
+        extern __shared__ __align__(16) unsigned char g_dyn_smem_mb[];
+        ring = reinterpret_cast<T *>(g_dyn_smem_mb) + (size_t)wp * RingB<T, VEC>::per_warp(D);
+        yb = ring + (D + 1) * RingB<T, VEC>::NF * NB;
+        wb = yb + NB;
+    } else {
+        __shared__ __align__(16) T sy[kWarps][NB];
+        __shared__ __align__(16) T sw[kWarps][NB];
+        __shared__ __align__(16) T sa[kWarps][NB];
+        yb = sy[wp];
+        wb = sw[wp];
+        ab = sa[wp];
+    }
     for (unsigned c = next_task(&m.msc->task_ctr[1], lane); c < m.total_tasks;
          c = next_task(&m.msc->task_ctr[1], lane)) {
         const unsigned t = m.total_tasks - 1u - c;    // reverse of phase A's order (L2 reuse)
@@ -185,10 +214,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
         k = __shfl_sync(0xffffffffu, k, 0);
         alpha = __shfl_sync(0xffffffffu, alpha, 0);
         double val[2] = {0.0, 0.0};
-        if (!done)
-            run_task_b<T, VEC, false>(d, task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz), k,
-                                      (T)alpha, sy[wp], sw[wp], sa[wp],
-                                          lane, val);
+        if (!done) {
+            const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
+            if constexpr (D > 0)
+                run_task_b_staged<T, VEC, TY, false, D, true>(d, tk, k, (T)alpha, ring, yb, wb, lane, val);
+            else
+                run_task_b<T, VEC, false>(d, tk, k, (T)alpha, yb, wb, ab, lane, val);
+        }
         publish_task<2>(val, m.partials, t, lane);
         double tot[2];
         if (group_complete<2>(m, g, t, lane, tot) && lane == 0 && !done)   // active all launch

@@ -743,7 +743,7 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
 
     const void *kb_init = (const void *)k_phase_b<double, VEC, TY, MINB, true, 0>;
     const int grid_b = phase_grid(kb_init, ntiles, ctx->num_sms);
-    const int grid_m = phase_grid((const void *)k_mphase_b<double, VEC, TY, MINB>, total, ctx->num_sms);
+    const int grid_m = phase_grid((const void *)k_mphase_b<double, VEC, TY, MINB, 0>, total, ctx->num_sms);
     // start: r0 = S_k - A_k p0, z0, d0 and the first criterion test, per condition
     for (int k = 0; k < K; ++k) {
         k_reset<<<1, 32, 0, s>>>(gsc + k, 0);
@@ -759,8 +759,8 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
         GMAF_CUDA(cudaMemsetAsync(msc, 0, sizeof(Scalars), s));
         for (long long it = 0; it <= (long long)opts->max_iter + 2 * kAsyncChunk; it += kAsyncChunk) {
             for (int q = 0; q < kAsyncChunk; ++q) {
-                k_mphase_a<double, VEC, TY, MINB><<<grid_m, kThreads, 0, s>>>(d_m);
-                k_mphase_b<double, VEC, TY, MINB><<<grid_m, kThreads, 0, s>>>(d_m);
+                k_mphase_a<double, VEC, TY, MINB, 0><<<grid_m, kThreads, 0, s>>>(d_m);
+                k_mphase_b<double, VEC, TY, MINB, 0><<<grid_m, kThreads, 0, s>>>(d_m);
             }
             GMAF_CUDA(cudaGetLastError());
             GMAF_CUDA(cudaMemcpyAsync(done_h, &msc->done, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -13,6 +13,7 @@
 // each group over its own tasks in task order, so a request's result is the
 // same whether it runs alone or among others.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -29,6 +30,32 @@ namespace gmaf {
 // decomposition of a request must not depend on what else is running.
 constexpr int kSvVec = 4, kSvTY = 32, kSvMinB = 2;
 constexpr int kSvW = 32 * kSvVec;
+constexpr int kSvStage = 2;            // rows staged ahead by cp.async (0: register prefetch)
+
+// The two batched phase kernels of the server and their dynamic shared memory.
+struct SvKernels {
+    const void *a, *b;
+    size_t smem_a, smem_b;
+};
+
+static SvKernels sv_kernels(bool staged)
+{
+    if (!staged)
+        return {(const void *)k_mphase_a<float, kSvVec, kSvTY, kSvMinB, 0>,
+                (const void *)k_mphase_b<float, kSvVec, kSvTY, kSvMinB, 0>, 0, 0};
+    SvKernels k{(const void *)k_mphase_a<float, kSvVec, kSvTY, kSvMinB, kSvStage>,
+                (const void *)k_mphase_b<float, kSvVec, kSvTY, kSvMinB, kSvStage>,
+                (size_t)kWarps * RingA<float, kSvVec>::per_warp(kSvStage) * sizeof(float),
+                (size_t)kWarps * RingB<float, kSvVec>::per_warp(kSvStage) * sizeof(float)};
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_a);
+        cudaFuncSetAttribute(k.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_b);
+        cudaGetLastError();
+        attr = true;
+    }
+    return k;
+}
 
 // ------------------------------------------------------------------ arena
 
@@ -172,6 +199,7 @@ struct gmaf_server {
     bool dirty;
     MultiDesc<float> hm;
     int grid_m;
+    SvKernels kern;
 };
 
 namespace gmaf {
@@ -448,11 +476,13 @@ static int rebuild_table(gmaf_server *sv)
         e = cudaMemcpyAsync(sv->d_mdesc, &hm, sizeof(MultiDesc<float>), cudaMemcpyHostToDevice, sv->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&sv->msc->done, 0, sizeof(int), sv->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)k_mphase_b<float, kSvVec, kSvTY, kSvMinB>, kThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
+    int per_sm = 0, per_sm_a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv->kern.b, kThreads, sv->kern.smem_b) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, sv->kern.a, kThreads, sv->kern.smem_a) !=
+            cudaSuccess)
+        per_sm = per_sm_a = 1;
+    per_sm = std::max(1, std::min(per_sm, per_sm_a));
     long long gm = ((long long)acc + kWarps - 1) / kWarps;
     if (gm > (long long)per_sm * sv->num_sms) gm = (long long)per_sm * sv->num_sms;
     if (gm < 1) gm = 1;
@@ -568,6 +598,8 @@ int gmaf_server_create(gmaf_ctx *ctx, size_t hbm_budget_bytes, gmaf_server **out
     sv->dirty = true;
     sv->hm = MultiDesc<float>{};
     sv->grid_m = 1;
+    const char *stg = std::getenv("GMAF_SV_STAGED");
+    sv->kern = sv_kernels(!(stg && std::atoi(stg) == 0));
     cudaError_t e = cudaMalloc(&sv->base, sv->budget);
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_mdesc, sizeof(MultiDesc<float>));
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_groups, kMaxGroups * sizeof(PcgDesc<float>));
@@ -659,11 +691,16 @@ int gmaf_server_run(gmaf_server *sv, int32_t iterations, int32_t *active_out, in
         if (sv->dirty && (st = rebuild_table(sv))) return st;
         cudaError_t e0 = cudaMemsetAsync(&sv->msc->done, 0, sizeof(int), sv->stream);
         if (e0 != cudaSuccess) return cuda_status(e0);
-        for (int it = 0; it < iterations; ++it) {
-            k_mphase_a<float, kSvVec, kSvTY, kSvMinB><<<sv->grid_m, kThreads, 0, sv->stream>>>(sv->d_mdesc);
-            k_mphase_b<float, kSvVec, kSvTY, kSvMinB><<<sv->grid_m, kThreads, 0, sv->stream>>>(sv->d_mdesc);
+        void *args[] = {(void *)&sv->d_mdesc};
+        cudaError_t e = cudaSuccess;
+        for (int it = 0; it < iterations && e == cudaSuccess; ++it) {
+            e = cudaLaunchKernel(sv->kern.a, dim3(sv->grid_m), dim3(kThreads), args, sv->kern.smem_a,
+                                 sv->stream);
+            if (e == cudaSuccess)
+                e = cudaLaunchKernel(sv->kern.b, dim3(sv->grid_m), dim3(kThreads), args, sv->kern.smem_b,
+                                     sv->stream);
         }
-        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
     }
     if ((st = harvest(sv))) return st;

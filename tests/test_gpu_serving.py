@@ -55,7 +55,11 @@ def run_all(g, ctx, its, budget=8 << 30, eps=1e-11, round_iters=32):
     return [res[k] for k in range(len(its))], max_active
 
 
-def test_served_step_matches_oracle(g, ctx):
+@pytest.mark.parametrize("staged", ["1", "0"])
+def test_served_step_matches_oracle(g, ctx, monkeypatch, staged):
+    """Both forms of the batched phase kernels: rows staged by cp.async and
+    register prefetch (the server picks its kernels when it is created)."""
+    monkeypatch.setenv("GMAF_SV_STAGED", staged)
     it = items([(96, 48, True)], seed=3)[0]
     (r,), _ = run_all(g, ctx, [it], eps=1e-12)
     o = oracle.picard_step(96, 48, PHYS, it.tex, it.state, it.state[:4], 2.7777777777777778e-4,
