@@ -106,13 +106,13 @@ static KernelSet<T> ks_staged()
             100000 * D + 1000 * VEC + 10 * TY + MINB, smem, 0};
 }
 
-// Both phases staged D rows ahead; id + 300000 D.
-template <typename T, int VEC, int TY, int MINB, int D>
+// Phase A staged DA rows ahead and phase B DB rows ahead; id + 200000 DA + 100000 DB.
+template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
 static KernelSet<T> ks_staged_ab()
 {
-    KernelSet<T> ks = ks_staged<T, VEC, TY, MINB, D>();
-    const size_t smem = (size_t)kWarps * RingA<T, VEC>::per_warp(D) * sizeof(T);
-    const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, D>;
+    KernelSet<T> ks = ks_staged<T, VEC, TY, MINB, DB>();
+    const size_t smem = (size_t)kWarps * RingA<T, VEC>::per_warp(DA) * sizeof(T);
+    const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA>;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -121,7 +121,7 @@ static KernelSet<T> ks_staged_ab()
     }
     ks.a = a;
     ks.smem_a = smem;
-    ks.id += 200000 * D;
+    ks.id += 200000 * DA;
     return ks;
 }
 
