@@ -216,9 +216,20 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
         double val[2] = {0.0, 0.0};
         if (!done) {
             const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
-            if constexpr (D > 0)
-                run_task_b_staged<T, VEC, TY, false, D, true>(d, tk, k, (T)alpha, ring, yb, wb, lane, val);
-            else
+            if constexpr (D > 0) {
+                // FP64: interior tiles take the body without the periodic-wrap tests
+                if constexpr (sizeof(T) == 8) {
+                    if (tk.i0 >= 2 && tk.i0 + W + 2 <= d.nth)
+                        run_task_b_staged<T, VEC, TY, false, D, false>(d, tk, k, (T)alpha, ring, yb, wb,
+                                                                       lane, val);
+                    else
+                        run_task_b_staged<T, VEC, TY, false, D, true>(d, tk, k, (T)alpha, ring, yb, wb,
+                                                                      lane, val);
+                } else {
+                    run_task_b_staged<T, VEC, TY, false, D, true>(d, tk, k, (T)alpha, ring, yb, wb, lane,
+                                                                  val);
+                }
+            } else
                 run_task_b<T, VEC, false>(d, tk, k, (T)alpha, yb, wb, ab, lane, val);
         }
         publish_task<2>(val, m.partials, t, lane);

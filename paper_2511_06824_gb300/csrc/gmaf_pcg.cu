@@ -632,7 +632,8 @@ constexpr int kAsyncChunk = 32;
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-template <int VEC, int TY, int MINB>
+// DB > 0: phase B staged DB rows ahead (VEC = 2).
+template <int VEC, int TY, int MINB, int DB>
 static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot_host,
                          const double *D, const double *invD, const double *aE, const double *aN,
                          const double *S, double *p, const gmaf_solver_opts *opts,
@@ -743,7 +744,19 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
 
     const void *kb_init = (const void *)k_phase_b<double, VEC, TY, MINB, true, 0>;
     const int grid_b = phase_grid(kb_init, ntiles, ctx->num_sms);
-    const int grid_m = phase_grid((const void *)k_mphase_b<double, VEC, TY, MINB, 0>, total, ctx->num_sms);
+    const void *kma = (const void *)k_mphase_a<double, VEC, TY, MINB, 0>;
+    const void *kmb = (const void *)k_mphase_b<double, VEC, TY, MINB, DB>;
+    const size_t smem_b = DB > 0 ? (size_t)kWarps * RingB<double, VEC>::per_warp(DB) * sizeof(double) : 0;
+    if (DB > 0) {
+        static bool attr = false;
+        if (!attr) {
+            GMAF_CUDA(cudaFuncSetAttribute(kmb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+            attr = true;
+        }
+    }
+    const int grid_m = std::min(phase_grid(kma, total, ctx->num_sms),
+                                phase_grid(kmb, total, ctx->num_sms, smem_b));
+    void *margs[] = {(void *)&d_m};
     // start: r0 = S_k - A_k p0, z0, d0 and the first criterion test, per condition
     for (int k = 0; k < K; ++k) {
         k_reset<<<1, 32, 0, s>>>(gsc + k, 0);
@@ -759,8 +772,8 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
         GMAF_CUDA(cudaMemsetAsync(msc, 0, sizeof(Scalars), s));
         for (long long it = 0; it <= (long long)opts->max_iter + 2 * kAsyncChunk; it += kAsyncChunk) {
             for (int q = 0; q < kAsyncChunk; ++q) {
-                k_mphase_a<double, VEC, TY, MINB, 0><<<grid_m, kThreads, 0, s>>>(d_m);
-                k_mphase_b<double, VEC, TY, MINB, 0><<<grid_m, kThreads, 0, s>>>(d_m);
+                GMAF_CUDA(cudaLaunchKernel(kma, dim3(grid_m), dim3(kThreads), margs, 0, s));
+                GMAF_CUDA(cudaLaunchKernel(kmb, dim3(grid_m), dim3(kThreads), margs, smem_b, s));
             }
             GMAF_CUDA(cudaGetLastError());
             GMAF_CUDA(cudaMemcpyAsync(done_h, &msc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -877,8 +890,8 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         if (opts->criterion == 1) {
             const bool vec = (nth % 2) == 0;     // 16-byte rows of doubles in every condition
             const double *iv = (const double *)ctx->buf[B_INVD];
-            return vec ? solve_async64<2, 32, 2>(ctx, nth, nz, K, cslot_host, D, iv, aE, aN, S, p, opts, info)
-                       : solve_async64<1, 32, 3>(ctx, nth, nz, K, cslot_host, D, iv, aE, aN, S, p, opts, info);
+            return vec ? solve_async64<2, 32, 2, 2>(ctx, nth, nz, K, cslot_host, D, iv, aE, aN, S, p, opts, info)
+                       : solve_async64<1, 32, 3, 0>(ctx, nth, nz, K, cslot_host, D, iv, aE, aN, S, p, opts, info);
         }
         PcgRun<double> run{};
         PcgDesc<double> &h = run.h;
