@@ -148,6 +148,11 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     const char *ie = std::getenv("GMAF_INNER_EPS");
     c->inner_floor = ie ? std::atof(ie) : 5e-7;
     if (!(c->inner_floor > 0.0 && c->inner_floor < 0.5)) c->inner_floor = 5e-7;
+    const char *mr = std::getenv("GMAF_MIXED_RESTART");
+    c->mixed_restart = (mr && std::atoi(mr) != 0) ? 1 : 0;
+    const char *rdl = std::getenv("GMAF_RELIABLE_DELTA");
+    c->reliable_delta = rdl ? std::atof(rdl) : 0.1;
+    if (!(c->reliable_delta > 0.0 && c->reliable_delta < 0.5)) c->reliable_delta = 0.1;
     *out = c;
     return GMAF_OK;
 }

@@ -43,6 +43,8 @@ struct Scalars {
     double rnorm;           // mixed precision: norm of the FP64 outer residual
     int iter, first, done, converged, status, pending, guard, zero_rhs;
     int max_iter;
+    int cont;               // mixed precision: the next initial pass continues the recurrence
+    double cscale;          //   (reliable update) with the old direction rescaled by cscale
     unsigned int ticket[6];
     unsigned int task_ctr[2];   // next task of phase A / phase B
 };
@@ -143,6 +145,8 @@ struct gmaf_ctx {
     int ntune, tune_next;
     int pp_nth, pp_nz, pp_K;       // shape of the Picard-step fields held in B_PP
     double inner_floor;            // smallest relative residual asked of an inner FP32 solve
+    int mixed_restart;             // restart the inner FP32 PCG at each refinement (else continue it)
+    double reliable_delta;         // continued recurrence: residual reduction between two refinements
 };
 
 namespace gmaf {

@@ -152,10 +152,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         if (!done) {
             const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
             if constexpr (D > 0)
-                val[0] = run_task_a_staged<T, VEC, TY, D>(d, tk, k, first != 0, (T)alpha, (T)beta, ring,
+                val[0] = run_task_a_staged<T, VEC, TY, D>(d, tk, k, first, (T)alpha, (T)beta, ring,
                                                           ub, ab, lane);
             else
-                val[0] = run_task_a<T, VEC, false>(d, tk, k, first != 0, (T)alpha, (T)beta, ub, ab, lane);
+                val[0] = run_task_a<T, VEC, false>(d, tk, k, first, (T)alpha, (T)beta, ub, ab, lane);
         }
         publish_task<1>(val, m.partials, t, lane);
         double tot[1];

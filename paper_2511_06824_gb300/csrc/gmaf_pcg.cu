@@ -517,10 +517,14 @@ struct PhaseClock {
 
 // [reset] [init_r] [init B] WHILE{A, B} [finalize], all on the stream.
 template <typename T>
-static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_iter, bool do_init_r)
+static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_iter, bool do_init_r,
+                    double cont_scale = 0.0)
 {
     cudaStream_t s = ctx->stream;
-    k_reset<<<1, 32, 0, s>>>(run.h.sc, keep_iter ? 1 : 0);
+    if (cont_scale > 0.0)
+        k_continue<<<1, 32, 0, s>>>(run.h.sc, cont_scale);
+    else
+        k_reset<<<1, 32, 0, s>>>(run.h.sc, keep_iter ? 1 : 0);
     GMAF_CUDA(cudaGetLastError());
     if (do_init_r) {
         k_init_r<T><<<run.grid_s, kThreads, 0, s>>>(run.d_desc);
@@ -1021,10 +1025,22 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     rd.r = (double *)ctx->buf[B_R64];
     GMAF_CUDA(cudaMemcpyAsync(d_rdesc, &rd, sizeof(ResidDesc), cudaMemcpyHostToDevice, s));
 
-    const double inner_floor = ctx->inner_floor;
-    const int max_outer = 12;
-    int total_inner = 0, outer = 0;
-    bool tuned = false;
+    // Refinement: p64 += the inner FP32 solution, r64 = S - A p64 in FP64, repeated
+    // until the FP64 residual meets eps.  By default the inner PCG is not
+    // restarted at a refinement: its residual is replaced by the FP64 one (a
+    // reliable update) and the recurrence continues with its direction u, so the
+    // Krylov information gathered so far is kept.  The residual is refreshed
+    // after every reduction by reliable_delta (GMAF_RELIABLE_DELTA, 0.1), before
+    // the FP32 recurrence drifts far from the true residual.  GMAF_MIXED_RESTART=1
+    // restarts the inner solve from each new residual instead, solving it down to
+    // the inner floor (GMAF_INNER_EPS) each time.
+    const bool continued = !ctx->mixed_restart;
+    const double inner_floor = continued ? ctx->reliable_delta : ctx->inner_floor;
+    const int max_outer = continued ? 200 : 12;
+    int total_inner = 0, outer = 0, longest = 0;
+    int last_iter = 0;          // the inner iteration counter at the end of the last solve
+    bool tuned = false, stalled = false;
+    double rnorm_prev = 0.0;
     inf.status = GMAF_NOT_CONVERGED;
     for (;;) {
         {
@@ -1061,19 +1077,30 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         if (eps_in < inner_floor) eps_in = inner_floor;
         if (eps_in > 0.5) eps_in = 0.5;
         h.eps = eps_in;
-        h.max_iter = opts->max_iter - total_inner;
+        const bool cont = outer > 0 && continued && rnorm_prev > 0.0 && !stalled;
+        // a continued recurrence keeps counting from where the last solve stopped;
+        // one that needs more than max(1000, 4 x the longest solve so far) for its
+        // reduction is cut off, and the next solve restarts from its residual
+        const int left = opts->max_iter - total_inner;
+        const int cap = std::max(1000, 4 * longest);
+        h.max_iter = cont ? last_iter + std::min(left, cap) : left;
         GMAF_TRY(prepare<float>(ctx, run, ctx->graph32));
-        GMAF_TRY(pcg_once<float>(ctx, run, ctx->graph32, false, true));
+        GMAF_TRY(pcg_once<float>(ctx, run, ctx->graph32, cont, true, cont ? rnorm_prev / ho->rnorm : 0.0));
+        rnorm_prev = ho->rnorm;
         k_update_p64<<<gs, kThreads, 0, s>>>(p, (const float *)ctx->buf[B_X32], N, dsc_outer);
         GMAF_CUDA(cudaGetLastError());
         GMAF_TRY(read_scalars(ctx, dsc, hsc));
-        total_inner += hsc->iter;
+        const int seg = cont ? hsc->iter - last_iter : hsc->iter;     // iterations of this solve
+        last_iter = hsc->iter;
+        total_inner += seg;
+        longest = std::max(longest, seg);
+        stalled = continued && !hsc->converged;
         ++outer;
         if (hsc->status != 0) {
             inf.status = hsc->status;
             break;
         }
-        if (hsc->iter == 0) break;     // no progress possible
+        if (seg == 0) break;     // no progress possible
     }
     inf.iterations = total_inner;
     inf.iterations_sum = total_inner * K;

@@ -426,11 +426,16 @@ struct RowA {
 // One task of phase A; returns the lane's share of the task's u.v.  UP marches
 // the rows from the top of the task down to its bottom (jend -> j0): the stencil
 // is symmetric in z, so only the roles of the two aN couplings swap.
+// first: 0 = p += alpha' u' and u = z + beta u'; 1 = u = z (initial iteration);
+// 2 = u = z + beta u' without the p update (first iteration after a reliable
+// update of the residual, whose p starts from zero).
 template <typename T, int VEC, bool UP>
-__device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk, int k, bool first,
+__device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk, int k, int first,
                                              T alpha_prev, T beta, T *ub, T *ab, int lane)
 {
     constexpr int W = 32 * VEC;
+    const bool uz = first == 1;      // u = z
+    const bool nop = first != 0;     // no p update
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
     const T *uo_base = d.u[(k + 1) & 1];
@@ -467,7 +472,7 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk
             }
             const size_t q0 = (size_t)jr * nth + g0;
             Vec<T, VEC>::ld(z + q0, R.z);
-            if (!first) {
+            if (!uz) {
                 Vec<T, VEC>::ld(uo + q0, R.uo);
             } else {
 #pragma unroll
@@ -477,7 +482,7 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk
             if (jr >= tk.j0 && jr < tk.jend) {
                 Vec<T, VEC>::ld(D + q0, R.D);
                 Vec<T, VEC>::ld(aE + q0, R.e);
-                if (!first && owned) {
+                if (!nop && owned) {
                     Vec<T, VEC>::ldrw(pp + q0, R.p);
                 } else {
 #pragma unroll
@@ -489,7 +494,7 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk
             }
             const size_t qh = (size_t)jr * nth + hg;
             R.hz = __ldg(z + qh);
-            R.huo = first ? T(0) : __ldg(uo + qh);
+            R.huo = uz ? T(0) : __ldg(uo + qh);
             R.he = __ldg(aE + qh);
         };
 
@@ -507,8 +512,8 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk
             if (jr != jlast) load_row(jr + step, nx);
             T u[VEC];
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) u[q] = first ? cur.z[q] : cur.z[q] + beta * cur.uo[q];
-            const T hu = first ? cur.hz : cur.hz + beta * cur.huo;
+            for (int q = 0; q < VEC; ++q) u[q] = uz ? cur.z[q] : cur.z[q] + beta * cur.uo[q];
+            const T hu = uz ? cur.hz : cur.hz + beta * cur.huo;
             // output row jo (the previous step's row): its u row and aE row are in
             // the shared buffers; u_m2 is the row beyond jo, u the row before it
             const int jo = jr - step;
@@ -533,7 +538,7 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk
                     const size_t qo = (size_t)jo * nth + g0;
                     Vec<T, VEC>::st(un + qo, u_m1);
                     Vec<T, VEC>::st(vv + qo, vout);
-                    if (!first) {
+                    if (!nop) {
                         T pn[VEC];
 #pragma unroll
                         for (int q = 0; q < VEC; ++q) pn[q] = p_m1[q] + alpha_prev * uo_m1[q];
@@ -610,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
         for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
              t = next_task(&sc->task_ctr[0], lane)) {
             const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
-            const double val[1] = {run_task_a<T, VEC, false>(d, tk, s_k, s_first != 0, (T)s_alpha,
+            const double val[1] = {run_task_a<T, VEC, false>(d, tk, s_k, s_first, (T)s_alpha,
                                                               (T)s_beta, su[wp], sa[wp], lane)};
             publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
         }
@@ -619,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
         const unsigned gw = blockIdx.x * kWarps + wp;
         double v = 0.0;
         static_pieces<true>(d.K, d.tiles_x, d.nz, W, d.sgroups, ntasks, gw, [&](const Task &tk) {
-            v += run_task_a<T, VEC, true>(d, tk, s_k, s_first != 0, (T)s_alpha, (T)s_beta, su[wp],
+            v += run_task_a<T, VEC, true>(d, tk, s_k, s_first, (T)s_alpha, (T)s_beta, su[wp],
                                           sa[wp], lane);
         });
         const double val[1] = {v};
@@ -840,8 +845,17 @@ __device__ __forceinline__ int finish_b(Scalars *sc, double rz, double rr, int k
     sc->rel = rel;
     int done = 0;
     if (INIT) {
+        // reliable update (mixed precision): r was replaced by the FP64 residual;
+        // continue with u = z + beta u', the old direction converted to the new
+        // units (old d = r.z of the last iteration, in units cscale times smaller)
+        if (sc->cont && finite_d(rz) && finite_d(sc->d) && sc->d > 0.0 && sc->cscale > 0.0) {
+            sc->beta = rz / (sc->cscale * sc->d);
+            sc->first = 2;
+        } else {
+            sc->first = 1;
+        }
+        sc->cont = 0;
         sc->d = rz;
-        sc->first = 1;
         sc->pending = 0;
         if (sc->zero_rhs) {
             sc->converged = 1;
@@ -998,10 +1012,30 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const PcgDesc<T> *__restr
         d.p[g] += alpha * u[g];
 }
 
+// Reliable update of the mixed-precision inner solve: keep the iteration count,
+// the direction u and d = r.z; the next initial pass continues the recurrence from
+// the new residual, whose units are cscale times those of the last one.
+static __global__ void k_continue(Scalars *sc, double cscale)
+{
+    if (threadIdx.x != 0) return;
+    sc->cont = 1;
+    sc->cscale = cscale;
+    sc->done = 0;
+    sc->converged = 0;
+    sc->status = 0;
+    sc->pending = 0;
+    sc->guard = 0;
+    sc->zero_rhs = 0;
+    for (int q = 0; q < 6; ++q) sc->ticket[q] = 0u;
+    sc->task_ctr[0] = 0u;
+    sc->task_ctr[1] = 0u;
+}
+
 static __global__ void k_reset(Scalars *sc, int keep_iter)
 {
     if (threadIdx.x != 0) return;
     if (!keep_iter) sc->iter = 0;
+    sc->cont = 0;
     sc->first = 1;
     sc->done = 0;
     sc->converged = 0;
@@ -1151,9 +1185,11 @@ struct RingA {
 
 template <typename T, int VEC, int TY, int D>
 __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const Task &tk, int k,
-                                                    bool first, T alpha_prev, T beta, T *ring,
+                                                    int first, T alpha_prev, T beta, T *ring,
                                                     T *ub, T *ab, int lane)
 {
+    const bool uz = first == 1;      // u = z (modes of `first` as in run_task_a)
+    const bool nop = first != 0;     // no p update
     constexpr int W = 32 * VEC;
     constexpr int NB = W + 8, NF = 6, SLOT = NF * NB;
     constexpr int CH = 16 / (int)sizeof(T);
@@ -1187,7 +1223,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             const bool in = jr >= tk.j0 && jr < tk.jend;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                if (first && (f == 1 || f == 5)) continue;     // no u', no p update
+                if ((uz && f == 1) || (nop && f == 5)) continue;     // no u' / no p update
                 if (!in && (f == 2 || f == 3 || f == 5)) continue;
                 if (!owned && f == 5) continue;
 #pragma unroll
@@ -1195,7 +1231,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             }
             if (lane < 2) {
                 cp_async_small<sizeof(T)>(slot + hs, src[0] + rq + hg);
-                if (!first) cp_async_small<sizeof(T)>(slot + NB + hs, src[1] + rq + hg);
+                if (!uz) cp_async_small<sizeof(T)>(slot + NB + hs, src[1] + rq + hg);
                 if (lane == 0) cp_async_small<sizeof(T)>(slot + 3 * NB + hs, src[3] + rq + hg);
             }
         }
@@ -1221,21 +1257,21 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
         T hz = T(0), huo = T(0), he = T(0);
         if (inrow) {
             Vec<T, VEC>::ldrw(cur + sown, zv);
-            if (!first) Vec<T, VEC>::ldrw(cur + NB + sown, uov);
+            if (!uz) Vec<T, VEC>::ldrw(cur + NB + sown, uov);
             Vec<T, VEC>::ldrw(cur + 4 * NB + sown, nv);
             if (in) {
                 Vec<T, VEC>::ldrw(cur + 2 * NB + sown, Dv);
                 Vec<T, VEC>::ldrw(cur + 3 * NB + sown, ev);
-                if (!first) Vec<T, VEC>::ldrw(cur + 5 * NB + sown, pv);
+                if (!nop) Vec<T, VEC>::ldrw(cur + 5 * NB + sown, pv);
             }
             hz = cur[hs];
-            if (!first) huo = cur[NB + hs];
+            if (!uz) huo = cur[NB + hs];
             he = cur[3 * NB + hs];
         }
         T u[VEC];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) u[q] = first ? zv[q] : zv[q] + beta * uov[q];
-        const T hu = first ? hz : hz + beta * huo;
+        for (int q = 0; q < VEC; ++q) u[q] = uz ? zv[q] : zv[q] + beta * uov[q];
+        const T hu = uz ? hz : hz + beta * huo;
         const int jo = jr - 1;
         if (jo >= tk.j0 && jo < tk.jend) {
             T vout[VEC];
@@ -1254,7 +1290,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
                 const size_t qo = (size_t)jo * nth + g0;
                 Vec<T, VEC>::st(un + qo, u_m1);
                 Vec<T, VEC>::st(vv + qo, vout);
-                if (!first) {
+                if (!nop) {
                     T pn[VEC];
 #pragma unroll
                     for (int q = 0; q < VEC; ++q) pn[q] = p_m1[q] + alpha_prev * uo_m1[q];
@@ -1319,7 +1355,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a_staged(const PcgDesc
     for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
          t = next_task(&sc->task_ctr[0], lane)) {
         const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
-        const double val[1] = {run_task_a_staged<T, VEC, TY, D>(d, tk, s_k, s_first != 0, (T)s_alpha,
+        const double val[1] = {run_task_a_staged<T, VEC, TY, D>(d, tk, s_k, s_first, (T)s_alpha,
                                                                 (T)s_beta, ring, ub, ab, lane)};
         publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
     }

@@ -113,3 +113,30 @@ def test_benchmark_workload_step_properties(g):
     delta = np.linalg.solve(Jd + DT * Je, -r["G"] - Je @ (e_prev + DT * w.state[4:] - w.state[:4]))
     np.testing.assert_allclose(r["state"][4:], w.state[4:] + delta, rtol=1e-9, atol=1e-18)
     np.testing.assert_allclose(r["state"][:4], e_prev + DT * r["state"][4:], rtol=1e-12)
+
+
+def test_benchmark_workload_refinement_modes(g, monkeypatch):
+    """The mixed-precision joint solve of the benchmark workload with the inner PCG
+    continued across refinements (default), restarted at each, and continued with
+    refinements too far apart (delta 1e-3: the FP32 recurrence drifts from the true
+    residual and a continued solve stalls; it is cut off and restarted).  All meet
+    Eq. 3.9 and give the same loads."""
+    w = inputs.make("textured-2048x1024-k9", 0)
+    out = {}
+    for name, restart, delta in (("continued", "0", "0.1"), ("restarted", "1", "0.1"),
+                                 ("far", "0", "0.001")):
+        monkeypatch.setenv("GMAF_MIXED_RESTART", restart)
+        monkeypatch.setenv("GMAF_RELIABLE_DELTA", delta)
+        with g.Context() as c:
+            r = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state,
+                                   w.state[:4], DT, F_EXT, w.d_e, w.d_edot,
+                                   g.solver_opts(eps=w.eps, precision=1))
+            info = g.gmaf_last_solve_info(c.handle)
+        assert r["status"] == 0, name
+        assert info["true_rel_residual"] <= w.eps, name
+        out[name] = (r, info)
+    it_c, it_r = out["continued"][1]["iterations"], out["restarted"][1]["iterations"]
+    assert it_c < it_r, (it_c, it_r)
+    assert out["far"][1]["iterations"] <= 4 * it_r
+    for name in ("restarted", "far"):
+        assert load_err(out[name][0]["loads"], out["continued"][0]["loads"]) <= 1e-6, name

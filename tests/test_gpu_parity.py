@@ -174,6 +174,29 @@ def test_mixed_precision_solve_matches_fp64_oracle(g, ctx, nth, nz, K, precond):
     assert info["outer_iterations"] >= 2
 
 
+@pytest.mark.parametrize("restart,delta", [("1", "0.1"), ("0", "0.1"), ("0", "0.3"), ("0", "0.001")])
+def test_mixed_refinement_modes_match_fp64_oracle(g, monkeypatch, restart, delta):
+    """FP64 refinement around the FP32 PCG, both ways: restarting the inner solve
+    from each FP64 residual, and continuing its recurrence with the FP64 residual
+    swapped in (reliable updates every reduction by delta)."""
+    monkeypatch.setenv("GMAF_MIXED_RESTART", restart)
+    monkeypatch.setenv("GMAF_RELIABLE_DELTA", delta)
+    nth, nz, K = 132, 45, 9
+    conds = states(K, seed=19)
+    c = g.Context()
+    try:
+        p, it, rel, po, ito, _ = solve_both(g, c.handle, nth, nz, tex_dimples(), conds, precision=1)
+        info = g.gmaf_last_solve_info(c.handle)
+    finally:
+        c.close()
+    assert rel <= 1e-10
+    assert rel_l2(p, po) <= 1e-6
+    assert info["outer_iterations"] >= 2
+    # the continued recurrence needs about the FP64 iteration count
+    if restart == "0" and delta != "0.001":
+        assert it <= 1.1 * ito + 10, (it, ito)
+
+
 def test_warm_start_zero_rhs_budget_and_invalid(g, ctx):
     nth, nz = 64, 32
     conds = states(2, seed=3)
