@@ -132,6 +132,11 @@ struct Request {
     PcgDesc<float> h;
     ResidDesc rd;
     int outer, total_inner, grid_s;
+    // continued inner recurrence (reliable updates, as in the joint solve)
+    double rnorm_prev;            // norm of the FP64 residual the last inner solve started from
+    int last_iter, longest;       // inner iteration counter after the last solve; longest solve
+    bool cont_run, stalled;       // the last solve continued the recurrence; it stalled
+    bool no_progress;             // the last solve made no iteration
 };
 
 constexpr size_t kHdrBytes = 8192;   // scalars, descriptors, conditions, flags, loads, result
@@ -249,21 +254,36 @@ static void carve(gmaf_server *sv, Request *r)
 }
 
 static constexpr double kInnerFloor = 5e-7;
-static constexpr int kMaxOuter = 12;
+static constexpr int kMaxOuter = 12;            // refinements when each restarts the inner solve
+static constexpr int kMaxOuterContinued = 200;  // refinements of a continued inner recurrence
 
 // Start (or restart) the inner FP32 solve of a request from its current r64.
-static int start_inner(gmaf_server *sv, Request *r, double true_rel)
+// Next inner solve of a request from its FP64 residual (norm rnorm, relative
+// true_rel).  As in the joint solve, the inner recurrence continues across
+// refinements (its residual replaced by the FP64 one after every reduction by
+// the context's reliable_delta) unless the context asks for restarts or the last
+// continued solve stalled.
+static int start_inner(gmaf_server *sv, Request *r, double true_rel, double rnorm)
 {
     cudaStream_t s = sv->stream;
+    const bool continued = !sv->ctx->mixed_restart;
     double eps_in = 0.5 * r->in.eps / true_rel;
-    if (eps_in < kInnerFloor) eps_in = kInnerFloor;
+    const double floor_in = continued ? sv->ctx->reliable_delta : kInnerFloor;
+    if (eps_in < floor_in) eps_in = floor_in;
     if (eps_in > 0.5) eps_in = 0.5;
     r->h.eps = eps_in;
-    r->h.max_iter = r->in.max_iter - r->total_inner;
+    const bool cont = continued && r->outer > 0 && !r->stalled && r->rnorm_prev > 0.0;
+    const int left = r->in.max_iter - r->total_inner;
+    r->h.max_iter = cont ? r->last_iter + std::min(left, std::max(1000, 4 * r->longest)) : left;
     cudaError_t e = cudaMemcpyAsync(r->d_desc, &r->h, sizeof(PcgDesc<float>), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
     k_make_b32<<<r->grid_s, kThreads, 0, s>>>(r->r64, r->b32, r->N, r->sc_out);
-    k_reset<<<1, 32, 0, s>>>(r->sc_in, 0);
+    if (cont)
+        k_continue<<<1, 32, 0, s>>>(r->sc_in, r->rnorm_prev / rnorm);
+    else
+        k_reset<<<1, 32, 0, s>>>(r->sc_in, 0);
+    r->cont_run = cont;
+    r->rnorm_prev = rnorm;
     k_init_r<float><<<r->grid_s, kThreads, 0, s>>>(r->d_desc);
     const int gb = (int)std::min<long long>((r->ntasks + kWarps - 1) / kWarps, (long long)sv->num_sms * kSvMinB);
     k_phase_b<float, kSvVec, kSvTY, kSvMinB, true, 0><<<gb, kThreads, 0, s>>>(r->d_desc);
@@ -351,8 +371,11 @@ static int admit(gmaf_server *sv, Request *r)
     if (e != cudaSuccess) return cuda_status(e);
     r->outer = 0;
     r->total_inner = 0;
+    r->rnorm_prev = 0.0;
+    r->last_iter = r->longest = 0;
+    r->cont_run = r->stalled = r->no_progress = false;
     if (ho.normS == 0.0 || !std::isfinite(ho.true_rel) || ho.true_rel <= r->in.eps) return 1;
-    return start_inner(sv, r, ho.true_rel);
+    return start_inner(sv, r, ho.true_rel, ho.rnorm);
 }
 
 // Loads of the 9 conditions, Jacobian and update; result to the host.
@@ -512,7 +535,12 @@ static int harvest(gmaf_server *sv)
         k_finalize<float><<<r->grid_s, kThreads, 0, s>>>(r->d_desc);
         k_update_p64<<<r->grid_s, kThreads, 0, s>>>(r->p, r->x32, r->N, r->sc_out);
         k_resid64<<<r->grid_s, kThreads, 0, s>>>(r->d_rdesc);
-        r->total_inner += hs[g].iter;
+        const int seg = r->cont_run ? hs[g].iter - r->last_iter : hs[g].iter;
+        r->last_iter = hs[g].iter;
+        r->total_inner += seg;
+        r->longest = std::max(r->longest, seg);
+        r->stalled = !sv->ctx->mixed_restart && !hs[g].converged;
+        r->no_progress = seg == 0;
         ended.push_back(g);
     }
     if (ended.empty()) return GMAF_OK;
@@ -539,7 +567,8 @@ static int harvest(gmaf_server *sv)
                 finish = true;
             } else if (o.normS == 0.0 || o.true_rel <= r->in.eps) {
                 finish = true;
-            } else if (r->outer >= kMaxOuter || r->total_inner >= r->in.max_iter || in.iter == 0) {
+            } else if (r->outer >= (sv->ctx->mixed_restart ? kMaxOuter : kMaxOuterContinued) ||
+                       r->total_inner >= r->in.max_iter || r->no_progress) {
                 status = GMAF_NOT_CONVERGED;
                 finish = true;
             }
@@ -549,7 +578,7 @@ static int harvest(gmaf_server *sv)
                 sv->dirty = true;
                 continue;
             }
-            int st = start_inner(sv, r, o.true_rel);
+            int st = start_inner(sv, r, o.true_rel, o.rnorm);
             if (st != GMAF_OK) return st;
         }
         keep.push_back(r);
