@@ -85,6 +85,11 @@ typedef struct { double e[4], edot[4]; } gmaf_state;
  * precision: 0 FP64 throughout; 1 mixed - FP32 stencil, preconditioner and
  *   vector updates with dot products accumulated to FP64 accuracy, inside an
  *   FP64 iterative-refinement loop whose residual and stopping test are FP64.
+ *   By default the inner FP32 PCG is not restarted at a refinement: after every
+ *   tenfold reduction its residual is replaced by the FP64 residual and the
+ *   recurrence continues with its search direction (environment variables
+ *   GMAF_RELIABLE_DELTA for the reduction, GMAF_MIXED_RESTART=1 to restart
+ *   instead; both read when the context is created).
  * zero_init: 1 start from p = 0 (Table 1 step 1); 0 use the contents of p. */
 typedef struct {
     int32_t precond;
@@ -106,7 +111,7 @@ typedef struct {
  * gmaf_picard_step). */
 typedef struct {
     int32_t iterations;        /* PCG iterations (inner iterations summed in mixed mode) */
-    int32_t outer_iterations;  /* iterative-refinement sweeps (mixed), 1 in FP64          */
+    int32_t outer_iterations;  /* FP64 refinements (mixed), 1 in FP64                   */
     int32_t restarts;          /* restarts after a true-residual check failed            */
     int32_t status;
     double rel_residual;       /* recurrence relative residual at exit (FP64 mode)       */
@@ -247,7 +252,7 @@ int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, const double
                              const gmaf_solver_opts *opts, void *cuda_stream, int32_t *iters_out,
                              double *rel_res_out);
 
-/* ---- continuous-batching server (the benchmark spec serving pattern) ----------
+/* ---- continuous-batching server ---------------------------------------
  * Requests are single Picard iterations (as gmaf_picard_step, always in the
  * mixed-precision mode, ASSOR-II) of a 9-condition joint batch on their own
  * grid (n_theta must be a multiple of 4).  gmaf_server_submit queues a request;
