@@ -653,7 +653,6 @@ struct RowB {
 };
 
 // One task of phase B; writes the lane's shares of the task's r.z and r.r.
-// One task of phase B; writes the lane's shares of the task's r.z and r.r.
 // One body serves every task (a second, specialised copy of this unrolled body
 // measured slower: the kernel is sensitive to its code size).  In FP32 the halo
 // work is branch-free: every lane issues the halo loads, lanes 4..31 at lane

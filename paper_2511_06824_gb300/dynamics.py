@@ -13,7 +13,11 @@ them only); the march uses a synthetic side load from the swash plate, the
 chamber force times tan(10 deg) (swash angle of Table 8) scaled by `kappa`,
 acting at the case end of the gap (generalized force on e3).  The default
 kappa = 0.2 keeps the eccentricity below 0.6 c over a revolution of the oracle
-on a 48 x 24 grid with the seeded trapezoid pressure (bound asked: 0.8 c).
+on a 48 x 24 grid with the seeded trapezoid pressure (bound asked: 0.8 c).  The
+load always acts along +x and nothing in the model restores the centred
+position, so on finer textured grids the eccentricity keeps growing under load:
+on the textured 1024 x 512 gap it reaches the wall within the first revolution
+(shaft step 76 with kappa = 0.2, in FP64 as in mixed precision).
 
 Everything per Picard iteration runs on the device through the C ABI; this
 module is the host loop.  The pressure fields stay in the library's context and
