@@ -409,9 +409,11 @@ static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand
             if (ms < best_t[c]) best_t[c] = ms;
         }
     }
+    // a later candidate replaces the pick only when it is more than 1% faster, so
+    // that near-ties (within the timing noise) resolve to the earlier, preferred one
     int best_i = 0;
     for (int c = 1; c < ncand; ++c)
-        if (best_t[c] < best_t[best_i]) best_i = c;
+        if (best_t[c] < 0.99f * best_t[best_i]) best_i = c;
     *best_out = best_i;
     return GMAF_OK;
 }
