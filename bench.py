@@ -88,16 +88,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def alg_bytes_per_dof(precision: str, n_cond: int = 9, n_slots: int = 5):
-    """Algorithmic bytes per joint DOF per launch of each PCG phase.
+def alg_bytes_per_dof(precision: str, n_cond: int = 9, n_slots: int = 5, p_period: int = 1):
+    """Algorithmic bytes per joint DOF per launch of each PCG phase, averaged over
+    iterations.
 
-    phase A reads z, u', p and writes u, v, p; phase B reads r, v and writes r, z;
-    each phase reads three coefficient arrays (D, a_E, a_N in A; 1/D, a_E, a_N in B),
-    stored once per coefficient slot: 5 slots serve the 9 conditions because the
-    rate-perturbed conditions share the matrix of the base condition."""
+    phase A reads z, u' and writes u, v; it also reads and writes p, every
+    iteration (p_period 1), or every second iteration together with the direction
+    before u' (p_period 2: p += alpha'' u'' + alpha' u').  Phase B reads r, v and
+    writes r, z.  Each phase reads three coefficient arrays (D, a_E, a_N in A;
+    1/D, a_E, a_N in B), stored once per coefficient slot: 5 slots serve the 9
+    conditions because the rate-perturbed conditions share the matrix of the base
+    condition."""
     w = 4 if precision == "mixed" else 8
     coef = 3 * w * n_slots / n_cond
-    return {"phase_a": 6 * w + coef, "phase_b": 4 * w + coef}
+    p_bytes = 2 * w if p_period == 1 else 3 * w / 2
+    return {"phase_a": 4 * w + p_bytes + coef, "phase_b": 4 * w + coef}
 
 
 class ClockSampler:
@@ -300,7 +305,7 @@ def run_ours(args):
     ph = gmaf.gmaf_phase_timing(ctx.handle)
     gmaf.gmaf_set_phase_timing(ctx.handle, False)
     hbm, peak_kind = peaks()
-    bpd = alg_bytes_per_dof(args.precision)
+    bpd = alg_bytes_per_dof(args.precision, p_period=timed.info.get("p_update_period", 1))
     phases = {}
     for k in ("phase_a", "phase_b"):
         tot, cnt = ph[k]

@@ -117,13 +117,18 @@ typedef struct {
     double rel_residual;       /* recurrence relative residual at exit (FP64 mode)       */
     double true_rel_residual;  /* ||S - A p|| / ||S|| at exit, in FP64                   */
     int32_t kernel_variant;    /* PCG kernels used: 1000 VEC + 10 TY + MINB (columns per
-                                  lane, rows per task, blocks per SM); chosen per problem
-                                  shape by the autotuner on the first solve of that shape */
+                                  lane, rows per task, blocks per SM), + 100000 DB when
+                                  phase B stages its rows DB ahead through shared memory,
+                                  + 200000 DA when phase A does; 1000000 + 1000 VEC + MINB
+                                  for the static schedule.  Chosen per problem shape by
+                                  the autotuner on the first solve of that shape */
     int32_t tasks;             /* strip x row-block x condition tasks per PCG phase       */
     int32_t iterations_sum;    /* PCG iterations summed over the conditions: n_cond x
                                   iterations under the synchronized criterion, the sum of
                                   the per-condition counts under the asynchronized one
                                   (iterations is then the largest of them)              */
+    int32_t p_update_period;   /* PCG iterations between two updates of p in phase A: 1,
+                                  or 2 when the staged FP32 phase A pairs them           */
 } gmaf_solve_info;
 
 typedef struct gmaf_ctx gmaf_ctx;

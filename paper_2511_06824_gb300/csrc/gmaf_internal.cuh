@@ -41,10 +41,12 @@ struct Scalars {
     double normS, rel, true_rel;
     double scale;           // mixed precision: FP32 matrix = scale * A
     double rnorm;           // mixed precision: norm of the FP64 outer residual
-    int iter, first, done, converged, status, pending, guard, zero_rhs;
+    int iter, first, done, converged, status, guard, zero_rhs;
+    int pending;            // alpha u terms not yet added to p (0, 1 or 2)
     int max_iter;
     int cont;               // mixed precision: the next initial pass continues the recurrence
     double cscale;          //   (reliable update) with the old direction rescaled by cscale
+    double alpha_pp;        // alpha of the older of two pending p updates (pending == 2)
     unsigned int ticket[6];
     unsigned int task_ctr[2];   // next task of phase A / phase B
 };

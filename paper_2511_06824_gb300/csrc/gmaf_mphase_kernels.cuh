@@ -134,34 +134,37 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
          t = next_task(&m.msc->task_ctr[0], lane)) {
         const int g = group_of(m.task_off, m.ngroups, t);
         const PcgDesc<T> &d = m.groups[g];
-        int done = 0, k = 0, first = 0;
+        int done = 0, k = 0, first = 0, pend = 0;
         double alpha = 0.0, beta = 0.0;
         if (lane == 0) {
             done = d.sc->done;
             k = d.sc->iter;
             first = d.sc->first;
+            pend = d.sc->pending;
             alpha = d.sc->alpha;
             beta = d.sc->beta;
         }
         done = __shfl_sync(0xffffffffu, done, 0);
         k = __shfl_sync(0xffffffffu, k, 0);
         first = __shfl_sync(0xffffffffu, first, 0);
+        pend = __shfl_sync(0xffffffffu, pend, 0);
         alpha = __shfl_sync(0xffffffffu, alpha, 0);
         beta = __shfl_sync(0xffffffffu, beta, 0);
         double val[1] = {0.0};
         if (!done) {
             const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
             if constexpr (D > 0)
-                val[0] = run_task_a_staged<T, VEC, TY, D>(d, tk, k, first, (T)alpha, (T)beta, ring,
-                                                          ub, ab, lane);
+                val[0] = run_task_a_staged<T, VEC, TY, D>(d, tk, k, first, pend, (T)alpha, T(0),
+                                                          (T)beta, ring, ub, ab, lane);
             else
-                val[0] = run_task_a<T, VEC, false>(d, tk, k, first, (T)alpha, (T)beta, ub, ab, lane);
+                val[0] = run_task_a<T, VEC, false>(d, tk, k, first, pend, (T)alpha, (T)beta, ub, ab,
+                                                   lane);
         }
         publish_task<1>(val, m.partials, t, lane);
         double tot[1];
         if (group_complete<1>(m, g, t, lane, tot) && lane == 0 && !done) {   // active all launch
             d.sc->guard += 1;
-            finish_a(d.sc, tot[0]);
+            finish_a(d.sc, tot[0], pend > 0);
         }
     }
     if (!last_block(&m.msc->ticket[kTicketA])) return;

@@ -76,6 +76,7 @@ struct KernelSet {
     size_t smem_b;             // dynamic shared memory of the phase-B kernels
     int sched;
     size_t smem_a;             // dynamic shared memory of the phase-A kernel
+    int p_period;              // iterations between two p updates of phase A (1 or 2)
 };
 
 // id = 1000 VEC + 10 TY + MINB (dynamic), 1000000 + 1000 VEC + MINB (static).
@@ -111,7 +112,7 @@ template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
 static KernelSet<T> ks_staged_ab()
 {
     KernelSet<T> ks = ks_staged<T, VEC, TY, MINB, DB>();
-    const size_t smem = (size_t)kWarps * RingA<T, VEC>::per_warp(DA) * sizeof(T);
+    const size_t smem = (size_t)kWarps * RingA<T, VEC, sizeof(T) == 4>::per_warp(DA) * sizeof(T);
     const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA>;
     static bool attr = false;
     if (!attr) {
@@ -122,6 +123,7 @@ static KernelSet<T> ks_staged_ab()
     ks.a = a;
     ks.smem_a = smem;
     ks.id += 200000 * DA;
+    ks.p_period = sizeof(T) == 4 ? 2 : 1;      // the staged FP32 phase A pairs the p updates
     return ks;
 }
 
@@ -841,6 +843,7 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
     inf.outer_iterations = 1;
     inf.kernel_variant = 1000 * VEC + 10 * TY + MINB;
     inf.tasks = (int)total;
+    inf.p_update_period = 1;
     *info = inf;
     return status;
 }
@@ -959,6 +962,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
             inf.outer_iterations = 1;
             inf.kernel_variant = run.ks.id;
             inf.tasks = (int)run.h.ntiles;
+            inf.p_update_period = std::max(1, run.ks.p_period);
             if (hsc->status != 0 || ho->status != 0) {
                 inf.status = hsc->status != 0 ? hsc->status : ho->status;
                 break;
@@ -1109,6 +1113,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     inf.outer_iterations = outer;
     inf.kernel_variant = run.ks.id;
     inf.tasks = (int)run.h.ntiles;
+    inf.p_update_period = std::max(1, run.ks.p_period);
     *info = inf;
     return inf.status;
 }

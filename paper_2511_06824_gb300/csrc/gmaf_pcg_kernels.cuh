@@ -426,16 +426,16 @@ struct RowA {
 // One task of phase A; returns the lane's share of the task's u.v.  UP marches
 // the rows from the top of the task down to its bottom (jend -> j0): the stencil
 // is symmetric in z, so only the roles of the two aN couplings swap.
-// first: 0 = p += alpha' u' and u = z + beta u'; 1 = u = z (initial iteration);
-// 2 = u = z + beta u' without the p update (first iteration after a reliable
-// update of the residual, whose p starts from zero).
+// first: 1 = u = z (initial iteration), else u = z + beta u' (2: first iteration
+// after a reliable update of the residual).  pend: alpha u terms not yet in p;
+// this body adds the pending one (p += alpha' u') whenever there is one.
 template <typename T, int VEC, bool UP>
 __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk, int k, int first,
-                                             T alpha_prev, T beta, T *ub, T *ab, int lane)
+                                             int pend, T alpha_prev, T beta, T *ub, T *ab, int lane)
 {
     constexpr int W = 32 * VEC;
     const bool uz = first == 1;      // u = z
-    const bool nop = first != 0;     // no p update
+    const bool nop = pend == 0;      // no p update
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
     const T *uo_base = d.u[(k + 1) & 1];
@@ -568,10 +568,14 @@ __device__ __forceinline__ double run_task_a(const PcgDesc<T> &d, const Task &tk
     return acc.value();
 }
 
-// Scalar update after the u.v reduction (alpha = d / u.v).
-__device__ __forceinline__ void finish_a(Scalars *sc, double uv)
+// Scalar update after the u.v reduction (alpha = d / u.v).  added: the phase
+// added the pending p updates; otherwise the last alpha stays pending as alpha_pp.
+__device__ __forceinline__ void finish_a(Scalars *sc, double uv, bool added)
 {
-    sc->pending = 0;
+    if (added)
+        sc->pending = 0;
+    else
+        sc->alpha_pp = sc->alpha;
     if (!finite_d(uv) || !(uv > 0.0) || !finite_d(sc->d)) {
         sc->status = GMAF_NONFINITE;
         sc->done = 1;
@@ -592,12 +596,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
     Scalars *sc = d.sc;
     __shared__ __align__(16) T su[kWarps][NB];
     __shared__ __align__(16) T sa[kWarps][NB];
-    __shared__ int s_done, s_k, s_first;
+    __shared__ int s_done, s_k, s_first, s_pend;
     __shared__ double s_alpha, s_beta;
     if (threadIdx.x == 0) {
         s_done = sc->done;
         s_k = sc->iter;
         s_first = sc->first;
+        s_pend = sc->pending;
         s_alpha = sc->alpha;
         s_beta = sc->beta;
         if (blockIdx.x == 0) {
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
         for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
              t = next_task(&sc->task_ctr[0], lane)) {
             const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
-            const double val[1] = {run_task_a<T, VEC, false>(d, tk, s_k, s_first, (T)s_alpha,
+            const double val[1] = {run_task_a<T, VEC, false>(d, tk, s_k, s_first, s_pend, (T)s_alpha,
                                                               (T)s_beta, su[wp], sa[wp], lane)};
             publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
         }
@@ -624,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
         const unsigned gw = blockIdx.x * kWarps + wp;
         double v = 0.0;
         static_pieces<true>(d.K, d.tiles_x, d.nz, W, d.sgroups, ntasks, gw, [&](const Task &tk) {
-            v += run_task_a<T, VEC, true>(d, tk, s_k, s_first, (T)s_alpha, (T)s_beta, su[wp],
+            v += run_task_a<T, VEC, true>(d, tk, s_k, s_first, s_pend, (T)s_alpha, (T)s_beta, su[wp],
                                           sa[wp], lane);
         });
         const double val[1] = {v};
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
     double tot[1];
     if (reduce_units<1>(reducer_of(d), ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
         threadIdx.x == 0)
-        finish_a(sc, tot[0]);
+        finish_a(sc, tot[0], s_pend > 0);
 }
 
 // ------------------------------------------------------------------ phase B
@@ -872,7 +877,7 @@ __device__ __forceinline__ int finish_b(Scalars *sc, double rz, double rr, int k
         const int it = k + 1;
         sc->iter = it;
         sc->first = 0;
-        sc->pending = 1;
+        sc->pending += 1;             // alpha u of this iteration
         if (!finite_d(rz) || !finite_d(rr)) {
             sc->status = GMAF_NONFINITE;
             done = 1;
@@ -996,19 +1001,27 @@ __global__ void __launch_bounds__(kThreads) k_init_r(const PcgDesc<T> *__restric
     }
 }
 
-// The update p += alpha u of the last iteration (deferred to phase A otherwise).
+// The p updates still pending after the last iteration (phase A adds them
+// otherwise): alpha u of the last iteration, and with two pending the one before
+// (alpha_pp, the other u buffer), added first.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_finalize(const PcgDesc<T> *__restrict__ dp)
 {
     const PcgDesc<T> &d = *dp;
     Scalars *sc = d.sc;
-    if (!sc->pending) return;
+    const int pend = sc->pending;
+    if (!pend) return;
     const T alpha = (T)sc->alpha;
+    const T alpha_pp = (T)sc->alpha_pp;
     const T *u = d.u[(sc->iter + 1) & 1];
+    const T *upp = d.u[sc->iter & 1];
     const long long N = d.n * d.K;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N;
-         g += (long long)gridDim.x * blockDim.x)
-        d.p[g] += alpha * u[g];
+         g += (long long)gridDim.x * blockDim.x) {
+        T x = d.p[g];
+        if (pend == 2) x += alpha_pp * upp[g];
+        d.p[g] = x + alpha * u[g];
+    }
 }
 
 // Reliable update of the mixed-precision inner solve: keep the iteration count,
@@ -1174,23 +1187,30 @@ __device__ __forceinline__ void cp_wait()
 // ahead.  A row's values move to registers (and the aE and u rows to their own
 // shared rows) when it is consumed, so the slot that the next copy overwrites is
 // never read again.
+//
+// PAIR: the p updates are applied every second iteration, two at a time
+// (p += alpha_pp u'' + alpha' u', u'' the direction before u', read from the u
+// buffer this phase overwrites, before it does): on average 2 fewer bytes per
+// unknown in FP32 than reading and writing p every iteration.
 
-template <typename T, int VEC>
+template <typename T, int VEC, bool PAIR = false>
 struct RingA {
-    static constexpr int W = 32 * VEC, NB = W + 8, NF = 6;
+    static constexpr int W = 32 * VEC, NB = W + 8, NF = PAIR ? 7 : 6;
     // elements per warp: (D+1) staged rows of NF fields, plus the u and aE rows
     __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
 };
 
-template <typename T, int VEC, int TY, int D>
+template <typename T, int VEC, int TY, int D, bool PAIR = false>
 __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const Task &tk, int k,
-                                                    int first, T alpha_prev, T beta, T *ring,
-                                                    T *ub, T *ab, int lane)
+                                                    int first, int pend, T alpha_prev, T alpha_pp,
+                                                    T beta, T *ring, T *ub, T *ab, int lane)
 {
     const bool uz = first == 1;      // u = z (modes of `first` as in run_task_a)
-    const bool nop = first != 0;     // no p update
+    // p updates: with PAIR only when two are pending (both added), else the pending one
+    const bool two = PAIR && pend == 2;
+    const bool nop = PAIR ? !two : pend == 0;
     constexpr int W = 32 * VEC;
-    constexpr int NB = W + 8, NF = 6, SLOT = NF * NB;
+    constexpr int NB = W + 8, NF = RingA<T, VEC, PAIR>::NF, SLOT = NF * NB;
     constexpr int CH = 16 / (int)sizeof(T);
     static_assert(VEC % CH == 0, "whole 16-byte chunks per lane");
     const int nth = d.nth, nz = d.nz;
@@ -1212,8 +1232,8 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
     const int hs = lane == 0 ? 3 : W + 4;
     const int hslot_u = lane < 2 ? hs : W + 7;
     const int hslot_a = lane == 0 ? hs : W + 7;
-    // fields: 0 z, 1 u', 2 D, 3 aE, 4 aN, 5 p
-    const T *src[NF] = {d.z + off, uo_base + off, d.D + coff, d.aE + coff, d.aN + coff, pp};
+    // fields: 0 z, 1 u', 2 D, 3 aE, 4 aN, 5 p (, 6 u'': the direction before u')
+    const T *src[7] = {d.z + off, uo_base + off, d.D + coff, d.aE + coff, d.aN + coff, pp, un};
 
     auto issue = [&](int jr) {
         if (jr >= 0 && jr < nz && jr >= tk.j0 - 1 && jr <= tk.jend) {
@@ -1223,8 +1243,9 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 if ((uz && f == 1) || (nop && f == 5)) continue;     // no u' / no p update
-                if (!in && (f == 2 || f == 3 || f == 5)) continue;
-                if (!owned && f == 5) continue;
+                if (f == 6 && !two) continue;
+                if (!in && (f == 2 || f == 3 || f >= 5)) continue;
+                if (!owned && f >= 5) continue;
 #pragma unroll
                 for (int c = 0; c < VEC; c += CH) cp_async16(slot + f * NB + sown + c, src[f] + rq + g0 + c);
             }
@@ -1238,9 +1259,10 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
     };
 
     T u_m1[VEC], u_m2[VEC], uo_m1[VEC], D_m1[VEC], e_m1[VEC], n_m1[VEC], n_m2[VEC], p_m1[VEC];
+    T upp_m1[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q)
-        u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = T(0);
+        u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = upp_m1[q] = T(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
     for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
@@ -1250,9 +1272,9 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
         const T *cur = ring + ((jr + 1) % (D + 1)) * SLOT;
         const bool inrow = jr >= 0 && jr < nz;
         const bool in = inrow && jr >= tk.j0 && jr < tk.jend;
-        T zv[VEC], uov[VEC], Dv[VEC], ev[VEC], nv[VEC], pv[VEC];
+        T zv[VEC], uov[VEC], Dv[VEC], ev[VEC], nv[VEC], pv[VEC], uppv[VEC];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) zv[q] = uov[q] = Dv[q] = ev[q] = nv[q] = pv[q] = T(0);
+        for (int q = 0; q < VEC; ++q) zv[q] = uov[q] = Dv[q] = ev[q] = nv[q] = pv[q] = uppv[q] = T(0);
         T hz = T(0), huo = T(0), he = T(0);
         if (inrow) {
             Vec<T, VEC>::ldrw(cur + sown, zv);
@@ -1262,6 +1284,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
                 Vec<T, VEC>::ldrw(cur + 2 * NB + sown, Dv);
                 Vec<T, VEC>::ldrw(cur + 3 * NB + sown, ev);
                 if (!nop) Vec<T, VEC>::ldrw(cur + 5 * NB + sown, pv);
+                if (two) Vec<T, VEC>::ldrw(cur + 6 * NB + sown, uppv);
             }
             hz = cur[hs];
             if (!uz) huo = cur[NB + hs];
@@ -1292,7 +1315,8 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
                 if (!nop) {
                     T pn[VEC];
 #pragma unroll
-                    for (int q = 0; q < VEC; ++q) pn[q] = p_m1[q] + alpha_prev * uo_m1[q];
+                    for (int q = 0; q < VEC; ++q)
+                        pn[q] = (two ? p_m1[q] + alpha_pp * upp_m1[q] : p_m1[q]) + alpha_prev * uo_m1[q];
                     Vec<T, VEC>::st(pp + qo, pn);
                 }
                 acc.add_row(rowsum);
@@ -1314,6 +1338,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             D_m1[q] = Dv[q];
             e_m1[q] = ev[q];
             p_m1[q] = pv[q];
+            upp_m1[q] = uppv[q];
         }
     }
     cp_wait<0>();
@@ -1321,21 +1346,25 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
     return acc.value();
 }
 
+// FP32: the p updates are paired (PAIR above); FP64 adds one every iteration.
 template <typename T, int VEC, int TY, int MINB, int D>
 __global__ void __launch_bounds__(kThreads, MINB) k_phase_a_staged(const PcgDesc<T> *__restrict__ dp)
 {
-    using R = RingA<T, VEC>;
+    constexpr bool PAIR = sizeof(T) == 4;
+    using R = RingA<T, VEC, PAIR>;
     constexpr int W = 32 * VEC;
     const PcgDesc<T> &d = *dp;
     Scalars *sc = d.sc;
     extern __shared__ __align__(16) unsigned char g_dyn_smem_a[];
-    __shared__ int s_done, s_k, s_first;
-    __shared__ double s_alpha, s_beta;
+    __shared__ int s_done, s_k, s_first, s_pend;
+    __shared__ double s_alpha, s_beta, s_alpha_pp;
     if (threadIdx.x == 0) {
         s_done = sc->done;
         s_k = sc->iter;
         s_first = sc->first;
+        s_pend = sc->pending;
         s_alpha = sc->alpha;
+        s_alpha_pp = sc->alpha_pp;
         s_beta = sc->beta;
         if (blockIdx.x == 0) {
             // stop unless phase B's last block asks for another iteration
@@ -1354,14 +1383,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a_staged(const PcgDesc
     for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
          t = next_task(&sc->task_ctr[0], lane)) {
         const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
-        const double val[1] = {run_task_a_staged<T, VEC, TY, D>(d, tk, s_k, s_first, (T)s_alpha,
-                                                                (T)s_beta, ring, ub, ab, lane)};
+        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR>(
+            d, tk, s_k, s_first, s_pend, (T)s_alpha, (T)s_alpha_pp, (T)s_beta, ring, ub, ab, lane)};
         publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
     }
     double tot[1];
     if (reduce_units<1>(reducer_of(d), ntasks, &sc->ticket[kTicketA], &sc->task_ctr[0], tot) &&
         threadIdx.x == 0)
-        finish_a(sc, tot[0]);
+        finish_a(sc, tot[0], PAIR ? s_pend == 2 : s_pend > 0);
 }
 
 template <typename T, int VEC>

@@ -66,7 +66,7 @@ class gmaf_solve_info(ctypes.Structure):
                 ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
                 ("kernel_variant", ctypes.c_int32), ("tasks", ctypes.c_int32),
-                ("iterations_sum", ctypes.c_int32)]
+                ("iterations_sum", ctypes.c_int32), ("p_update_period", ctypes.c_int32)]
 
 
 class gmaf_request(ctypes.Structure):

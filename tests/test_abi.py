@@ -72,6 +72,7 @@ int main(void) {
   P(gmaf_solver_opts, precision) P(gmaf_solver_opts, zero_init) P(gmaf_solver_opts, criterion)
   P(gmaf_solve_info, rel_residual) P(gmaf_solve_info, true_rel_residual)
   P(gmaf_solve_info, kernel_variant) P(gmaf_solve_info, tasks) P(gmaf_solve_info, iterations_sum)
+  P(gmaf_solve_info, p_update_period)
   P(gmaf_physics, p_case)
   return 0;
 }
