@@ -106,10 +106,12 @@ __device__ __forceinline__ bool last_block(unsigned *ticket)
 }
 
 // D > 0: the input rows are staged D rows ahead through a per-warp shared ring
-// (dynamic shared memory of kWarps * RingA<T, VEC>::per_warp(D) elements).
+// (dynamic shared memory of kWarps * RingA<T, VEC, PAIR>::per_warp(D) elements);
+// in FP32 the staged phase pairs the p updates as the joint kernel does.
 template <typename T, int VEC, int TY, int MINB, int D>
 __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> *__restrict__ mp)
 {
+    constexpr bool PAIR = D > 0 && sizeof(T) == 4;
     constexpr int W = 32 * VEC;
     constexpr int NB = W + 8;
     const MultiDesc<T> &m = *mp;
@@ -121,8 +123,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
     T *ring = nullptr, *ub, *ab;
     if constexpr (D > 0) {
         extern __shared__ __align__(16) unsigned char g_dyn_smem_ma[];
-        ring = reinterpret_cast<T *>(g_dyn_smem_ma) + (size_t)wp * RingA<T, VEC>::per_warp(D);
-        ub = ring + (D + 1) * RingA<T, VEC>::NF * NB;
+        ring = reinterpret_cast<T *>(g_dyn_smem_ma) + (size_t)wp * RingA<T, VEC, PAIR>::per_warp(D);
+        ub = ring + (D + 1) * RingA<T, VEC, PAIR>::NF * NB;
         ab = ub + NB;
     } else {
         __shared__ __align__(16) T su[kWarps][NB];
@@ -135,13 +137,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         const int g = group_of(m.task_off, m.ngroups, t);
         const PcgDesc<T> &d = m.groups[g];
         int done = 0, k = 0, first = 0, pend = 0;
-        double alpha = 0.0, beta = 0.0;
+        double alpha = 0.0, beta = 0.0, alpha_pp = 0.0;
         if (lane == 0) {
             done = d.sc->done;
             k = d.sc->iter;
             first = d.sc->first;
             pend = d.sc->pending;
             alpha = d.sc->alpha;
+            alpha_pp = d.sc->alpha_pp;
             beta = d.sc->beta;
         }
         done = __shfl_sync(0xffffffffu, done, 0);
@@ -149,13 +152,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         first = __shfl_sync(0xffffffffu, first, 0);
         pend = __shfl_sync(0xffffffffu, pend, 0);
         alpha = __shfl_sync(0xffffffffu, alpha, 0);
+        alpha_pp = __shfl_sync(0xffffffffu, alpha_pp, 0);
         beta = __shfl_sync(0xffffffffu, beta, 0);
         double val[1] = {0.0};
         if (!done) {
             const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
             if constexpr (D > 0)
-                val[0] = run_task_a_staged<T, VEC, TY, D>(d, tk, k, first, pend, (T)alpha, T(0),
-                                                          (T)beta, ring, ub, ab, lane);
+                val[0] = run_task_a_staged<T, VEC, TY, D, PAIR>(d, tk, k, first, pend, (T)alpha,
+                                                                (T)alpha_pp, (T)beta, ring, ub, ab, lane);
             else
                 val[0] = run_task_a<T, VEC, false>(d, tk, k, first, pend, (T)alpha, (T)beta, ub, ab,
                                                    lane);
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         double tot[1];
         if (group_complete<1>(m, g, t, lane, tot) && lane == 0 && !done) {   // active all launch
             d.sc->guard += 1;
-            finish_a(d.sc, tot[0], pend > 0);
+            finish_a(d.sc, tot[0], PAIR ? pend == 2 : pend > 0);
         }
     }
     if (!last_block(&m.msc->ticket[kTicketA])) return;

@@ -45,7 +45,7 @@ static SvKernels sv_kernels(bool staged)
                 (const void *)k_mphase_b<float, kSvVec, kSvTY, kSvMinB, 0>, 0, 0};
     SvKernels k{(const void *)k_mphase_a<float, kSvVec, kSvTY, kSvMinB, kSvStage>,
                 (const void *)k_mphase_b<float, kSvVec, kSvTY, kSvMinB, kSvStage>,
-                (size_t)kWarps * RingA<float, kSvVec>::per_warp(kSvStage) * sizeof(float),
+                (size_t)kWarps * RingA<float, kSvVec, true>::per_warp(kSvStage) * sizeof(float),
                 (size_t)kWarps * RingB<float, kSvVec>::per_warp(kSvStage) * sizeof(float)};
     static bool attr = false;
     if (!attr) {
