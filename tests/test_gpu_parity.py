@@ -197,6 +197,32 @@ def test_mixed_refinement_modes_match_fp64_oracle(g, monkeypatch, restart, delta
         assert it <= 1.1 * ito + 10, (it, ito)
 
 
+@pytest.mark.parametrize("n_iter", [1, 2, 3, 4, 5, 8, 9])
+def test_truncated_mixed_solve_matches_oracle_iterate(g, monkeypatch, n_iter):
+    """Stopped after n_iter PCG iterations (budget), the mixed solve's p is the
+    oracle's PCG iterate p_n to FP32 accuracy.  The staged FP32 phase A adds the p
+    updates two at a time, so odd and even n end with one or two updates still
+    pending for the finalize kernel; a lost or doubled update would be an O(1) error."""
+    monkeypatch.setenv("GMAF_VARIANT", "604322")
+    nth, nz, K = 260, 70, 3
+    conds = states(K, seed=23)
+    so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
+    p = zeros(K * nth * nz)
+    c = g.Context()
+    try:
+        opts = g.solver_opts(eps=1e-10, precision=1, max_iter=n_iter)
+        st, it, rel = g.gmaf_solve_joint(c.handle, nth, nz, K, dev(D), dev(aE), dev(aN), dev(S), p,
+                                         opts, allow_not_converged=True)
+        info = g.gmaf_last_solve_info(c.handle)
+    finally:
+        c.close()
+    assert st == -3 and it == n_iter
+    assert info["kernel_variant"] == 604322 and info["p_update_period"] == 2
+    sto, po, ito, _, _ = oracle.solve_joint(nth, nz, D, aE, aN, S, eps=1e-10, max_iter=n_iter)
+    assert ito == n_iter
+    assert rel_l2(host(p).reshape(K, nz, nth), po) <= 1e-5
+
+
 def test_warm_start_zero_rhs_budget_and_invalid(g, ctx):
     nth, nz = 64, 32
     conds = states(2, seed=3)
