@@ -58,7 +58,8 @@ struct PcgDesc {
     int nth, nz, K, tiles_x, tiles_y, precond, zero_init, use_cond;
     long long n, ntiles;
     long long sgroups;             // row groups of the static schedule
-    const T *D, *invD, *aE, *aN;   // coefficient slots, [slot][n]
+    const T *D, *invD, *aE, *aN;   // coefficient slots, [slot][n]; invD holds omega / D for
+                                   // ASSOR-II, 1 / D for Jacobi, the ASSOR-I diagonal for it
     const int *cslot;              // coefficient slot of each condition, [K]
     const T *b;                    // right-hand side, [K][n]
     T *p, *z, *v;

@@ -619,7 +619,8 @@ static void diag_inverse64(const gmaf_solver_opts *opts, const double *D, const 
         k_assor1_diag<double><<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, aE, aN, nth, nz, m,
                                                                           opts->omega, nullptr, out);
     else
-        k_invd64<<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, out, m);
+        k_invd64<<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, out, m,
+                                                               opts->precond == 1 ? opts->omega : 1.0);
 }
 
 // PCG-kernel preconditioner: ASSOR-II runs its two passes, Jacobi and ASSOR-I
@@ -993,7 +994,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     GMAF_TRY(ensure(ctx, B_R64, (size_t)N * sizeof(double)));
     k_to_f32<<<stream_grid(m, ctx->num_sms), kThreads, 0, s>>>(
         D, aE, aN, (float *)ctx->buf[B_D32], (float *)ctx->buf[B_INVD32], (float *)ctx->buf[B_AE32],
-        (float *)ctx->buf[B_AN32], m, dsc_outer);
+        (float *)ctx->buf[B_AN32], m, dsc_outer, opts->precond == 1 ? opts->omega : 1.0);
     if (opts->precond == 2)
         k_assor1_diag<float><<<stream_grid(m, ctx->num_sms), kThreads, 0, s>>>(
             D, aE, aN, nth, nz, m, opts->omega, dsc_outer, (float *)ctx->buf[B_INVD32]);

@@ -643,7 +643,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a(const PcgDesc<T> *__
 
 // ------------------------------------------------------------------ phase B
 //   r -= alpha v;  z = M^-1 r;  partial r.z, r.r
-// Marching: at row jr the warp forms r(jr), y = D^-1 r (shared row), the first
+// The stored diagonal d.invD is omega D^-1 for ASSOR-II (D^-1 for Jacobi), so y,
+// w and z below are omega times those of Eq. 3.5-3.6 (PCG is invariant under a
+// constant factor on the preconditioner, as it is under the c1 left out of z).
+// Marching: at row jr the warp forms r(jr), y = omega D^-1 r (shared row), the first
 // ASSOR pass w(jr) (needs y(jr - 1) in registers and the row neighbours of
 // y(jr)), and the second pass z(jr - 1) (needs w(jr) in registers and the row
 // neighbours of w(jr - 1), still in the shared row).  Halo columns i0 - 2 ..
@@ -672,7 +675,6 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
     constexpr bool BF = sizeof(T) == 4;
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
-    const T omega = d.omega;
     const bool assor = (d.precond == 1);
     const T *ro_base = d.r[k & 1];
     T *rn_base = d.r[(k + 1) & 1];
@@ -770,7 +772,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
                     if (gi > 0)                                                        // west
                         sum += ((q > 0) ? cur.e[q - 1] : ab[s - 1]) * ((q > 0) ? y[q - 1] : yb[s - 1]);
                     if (gi == nth - 1) sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);  // east, wrapped
-                    od[q] = omega * cur.dI[q];
+                    od[q] = cur.dI[q];
                     w[q] = y[q] + od[q] * sum;
                 }
                 // halo w (used for lanes 1, 2; in FP32 the others compute and discard it)
@@ -779,7 +781,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
                     if (jr > 0) sum += hn_m1 * hy_m1;
                     if (hg > 0) sum += ab[hs - 1] * yb[hs - 1];
                     if (hg == nth - 1) sum += cur.he * yb[hs + 1];
-                    hw = hy + omega * cur.hd * sum;
+                    hw = hy + cur.hd * sum;
                 }
             }
             // second pass on row jo = jr - 1: z = w + omega D^-1 (upper couplings) w.
@@ -1101,20 +1103,24 @@ static __global__ void __launch_bounds__(kThreads) k_resid64(const ResidDesc *__
     }
 }
 
-// 1/D for FP64 coefficient slots.
-static __global__ void k_invd64(const double *__restrict__ D, double *__restrict__ invD, long long m)
+// The stored diagonal of FP64 coefficient slots, w / D: w = omega for ASSOR-II, whose two passes then use
+// it as omega D^-1 directly (y, w and z come out scaled by omega, which PCG does
+// not see: alpha takes the inverse factor), w = 1 for Jacobi.
+static __global__ void k_invd64(const double *__restrict__ D, double *__restrict__ invD, long long m,
+                                double w)
 {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
          q += (long long)gridDim.x * blockDim.x)
-        invD[q] = 1.0 / D[q];
+        invD[q] = w / D[q];
 }
 
 // FP32 copies of the coefficient slots scaled by a power of two so that the
-// FP32 entries are of order one: A32 = scale * A.
+// FP32 entries are of order one: A32 = scale * A; the stored diagonal is w / D32
+// (w = omega for ASSOR-II, 1 for Jacobi, as k_invd64).
 static __global__ void k_to_f32(const double *__restrict__ D, const double *__restrict__ aE,
                          const double *__restrict__ aN, float *__restrict__ D32,
                          float *__restrict__ invD32, float *__restrict__ aE32,
-                         float *__restrict__ aN32, long long m, Scalars *sc)
+                         float *__restrict__ aN32, long long m, Scalars *sc, double w)
 {
     const double scale = ldexp(1.0, -ilogb(D[0]));
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->scale = scale;
@@ -1122,7 +1128,7 @@ static __global__ void k_to_f32(const double *__restrict__ D, const double *__re
          q += (long long)gridDim.x * blockDim.x) {
         const double dd = D[q] * scale;
         D32[q] = (float)dd;
-        invD32[q] = (float)(1.0 / dd);
+        invD32[q] = (float)(w / dd);
         aE32[q] = (float)(aE[q] * scale);
         aN32[q] = (float)(aN[q] * scale);
     }
@@ -1419,7 +1425,6 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     static_assert(VEC % CH == 0, "whole 16-byte chunks per lane");
     const int nth = d.nth, nz = d.nz;
     const long long n = d.n;
-    const T omega = d.omega;
     const bool assor = (d.precond == 1);
     RowAcc<T> arz, arr;
     const size_t off = (size_t)tk.cond * (size_t)n;
@@ -1521,14 +1526,14 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
                 const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
                 if (!EDGE || gi > 0) sum += aW * yW;
                 if (EDGE && gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
-                od[q] = omega * dI[q];
+                od[q] = dI[q];
                 w[q] = y[q] + od[q] * sum;
             }
             if (BF || lane == 1 || lane == 2) {
                 T sum = south ? hn_m1 * hy_m1 : T(0);
                 if (!EDGE || hg > 0) sum += ab[hs - 1] * yb[hs - 1];
                 if (EDGE && hg == nth - 1) sum += he * yb[hs + 1];
-                hw = hy + omega * hd * sum;
+                hw = hy + hd * sum;
             }
         }
         const int jo = jr - 1;

@@ -316,7 +316,8 @@ static int admit(gmaf_server *sv, Request *r)
         return st;
     const long long m = 5 * r->n;
     k_to_f32<<<stream_grid_s(m, sv->num_sms), kThreads, 0, s>>>(r->D, r->aE, r->aN, r->D32, r->invD32,
-                                                               r->aE32, r->aN32, m, r->sc_out);
+                                                               r->aE32, r->aN32, m, r->sc_out,
+                                                               r->in.omega);
     // inner solve descriptor
     PcgDesc<float> &h = r->h;
     h = PcgDesc<float>{};
