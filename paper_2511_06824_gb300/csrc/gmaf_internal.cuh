@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -155,6 +156,25 @@ struct gmaf_ctx {
 namespace gmaf {
 
 constexpr size_t kPinnedBytes = 64 * 1024;
+
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device.
+// The attribute is per device, so each call site keeps a mask of the device
+// ordinals it has set (ordinals from 64 on are set on every call).
+inline void smem_optin(std::atomic<unsigned long long> &done, const void *fn, size_t bytes)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load() & bit)) return;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+        cudaSuccess)
+        done.fetch_or(bit);
+    else
+        cudaGetLastError();
+}
 
 int ensure(gmaf_ctx *ctx, int id, size_t bytes);
 int cuda_status(cudaError_t e);

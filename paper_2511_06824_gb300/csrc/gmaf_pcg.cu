@@ -96,13 +96,9 @@ static KernelSet<T> ks_staged()
     const size_t smem = (size_t)kWarps * RingB<T, VEC>::per_warp(D) * sizeof(T);
     const void *b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, D>;
     const void *bi = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, D>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(bi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaGetLastError();
-        attr = true;
-    }
+    static std::atomic<unsigned long long> done_b{0}, done_bi{0};
+    smem_optin(done_b, b, smem);
+    smem_optin(done_bi, bi, smem);
     return {(const void *)k_phase_a<T, VEC, TY, MINB, 0>, b, bi, 32 * VEC, TY,
             100000 * D + 1000 * VEC + 10 * TY + MINB, smem, 0};
 }
@@ -114,12 +110,8 @@ static KernelSet<T> ks_staged_ab()
     KernelSet<T> ks = ks_staged<T, VEC, TY, MINB, DB>();
     const size_t smem = (size_t)kWarps * RingA<T, VEC, sizeof(T) == 4>::per_warp(DA) * sizeof(T);
     const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaGetLastError();
-        attr = true;
-    }
+    static std::atomic<unsigned long long> done_a{0};
+    smem_optin(done_a, a, smem);
     ks.a = a;
     ks.smem_a = smem;
     ks.id += 200000 * DA;
@@ -757,11 +749,8 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
     const void *kmb = (const void *)k_mphase_b<double, VEC, TY, MINB, DB>;
     const size_t smem_b = DB > 0 ? (size_t)kWarps * RingB<double, VEC>::per_warp(DB) * sizeof(double) : 0;
     if (DB > 0) {
-        static bool attr = false;
-        if (!attr) {
-            GMAF_CUDA(cudaFuncSetAttribute(kmb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-            attr = true;
-        }
+        static std::atomic<unsigned long long> done_mb{0};
+        smem_optin(done_mb, kmb, smem_b);
     }
     const int grid_m = std::min(phase_grid(kma, total, ctx->num_sms),
                                 phase_grid(kmb, total, ctx->num_sms, smem_b));

@@ -47,13 +47,9 @@ static SvKernels sv_kernels(bool staged)
                 (const void *)k_mphase_b<float, kSvVec, kSvTY, kSvMinB, kSvStage>,
                 (size_t)kWarps * RingA<float, kSvVec, true>::per_warp(kSvStage) * sizeof(float),
                 (size_t)kWarps * RingB<float, kSvVec>::per_warp(kSvStage) * sizeof(float)};
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k.a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_a);
-        cudaFuncSetAttribute(k.b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_b);
-        cudaGetLastError();
-        attr = true;
-    }
+    static std::atomic<unsigned long long> done_a{0}, done_b{0};
+    smem_optin(done_a, k.a, k.smem_a);
+    smem_optin(done_b, k.b, k.smem_b);
     return k;
 }
 
