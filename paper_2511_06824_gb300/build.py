@@ -39,8 +39,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     flags = _flags() + list(extra_flags or [])
 
+    # per-process object names: ranks that build at the same time never link
+    # each other's half-written objects (the library itself is replaced atomically)
     def one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, src.replace(".cu", f".{os.getpid()}.o"))
         cmd = [NVCC, "-c", os.path.join(CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -57,6 +59,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    for o in objs:
+        try:
+            os.remove(o)
+        except OSError:
+            pass
     return LIB
 
 
