@@ -13,6 +13,12 @@
  * the paper is silent the reading adopted is stated at the function (the same
  * readings are listed in the design notes of the repository).
  *
+ * Pins: every function is checked by the CPU test-suite against something other
+ * than itself - closed forms, dense library solves and factorisations, brute
+ * force, invariants and convergence orders.  None is checked against a worked
+ * numeric example of the paper, which prints none: the whole path is parity
+ * unpinned against the paper's own numbers.
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so gmaf_oracle.c -lm
  * (-ffp-contract=off: no fused multiply-add, so x86-64 and aarch64 give the
  * same bits.)
