@@ -118,6 +118,56 @@ def test_texture_raises_conductance_only_inside_dimples():
     assert 0.1 < frac < 0.3
 
 
+# ----------------------------------------------------------------------------- film rate
+
+
+def test_film_rate_is_the_derivative_of_the_film_along_the_rates():
+    """Eq. 2.3 with the chain rule: dh/dt = sum_i dh/de_i edot_i.  Pinned by a central
+    difference of the film itself along edot, h(e + d edot) - h(e - d edot) over 2 d,
+    at seeded points with four distinct rates (a swapped axial split of the rates,
+    e1 <-> e3 or e2 <-> e4, changes the result by about |edot_1 - edot_3|)."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for _ in range(50):
+        e = rng.uniform(-0.4 * C, 0.4 * C, 4)
+        ed = rng.uniform(-1e-4, 1e-4, 4)
+        theta = rng.uniform(0.0, 2 * math.pi)
+        z = rng.uniform(0.0, L)
+        d = 1e-5                                   # d * edot ~ 1e-9 m, well below c
+        fd = (oracle.film(PHYS, SMOOTH, e + d * ed, theta, z) -
+              oracle.film(PHYS, SMOOTH, e - d * ed, theta, z)) / (2 * d)
+        got = oracle.film_rate(PHYS, e, ed, theta, z)
+        worst = max(worst, abs(got - fd) / np.abs(ed).max())
+    assert worst < 1e-6
+    # the texture is static in the piston frame: it changes h, not dh/dt
+    e, ed = np.array([3e-6, -2e-6, 5e-6, 1e-6]), np.array([4e-5, -7e-5, 2e-5, 9e-5])
+    d = 1e-5
+    tex = tex_default()
+    for theta, z in [(0.3, 0.011), (2.0, 0.027), (4.4, 0.035)]:
+        fd = (oracle.film(PHYS, tex, e + d * ed, theta, z) -
+              oracle.film(PHYS, tex, e - d * ed, theta, z)) / (2 * d)
+        assert abs(oracle.film_rate(PHYS, e, ed, theta, z) - fd) < 1e-6 * 9e-5
+
+
+def test_film_rate_splits_the_rates_linearly_along_the_gap():
+    """At the chamber end (z = 0) only edot_1, edot_2 move the film, at the case end
+    only edot_3, edot_4, and at mid-gap each pair counts half."""
+    e = np.array([3e-6, -2e-6, 5e-6, 1e-6])
+    for theta in (0.0, 0.7, 1.9, 3.3):
+        for k in range(4):
+            ed = np.zeros(4)
+            ed[k] = 1e-4
+            at0 = oracle.film_rate(PHYS, e, ed, theta, 0.0)
+            atL = oracle.film_rate(PHYS, e, ed, theta, L)
+            if k < 2:
+                assert atL == 0.0 and at0 != 0.0
+            else:
+                assert at0 == 0.0 and atL != 0.0
+        # a pure tilt about mid-gap (edot_3 = -edot_1) leaves the mid-gap film still
+        ed = np.array([1e-4, -6e-5, -1e-4, 6e-5])
+        assert abs(oracle.film_rate(PHYS, e, ed, theta, 0.5 * L)) < 1e-20
+
+
 # ----------------------------------------------------------------------------- assembly
 
 
@@ -421,6 +471,64 @@ def test_rotation_by_whole_cells():
         np.testing.assert_allclose(lr[off:off + 2], R @ ld[off:off + 2], atol=1e-8 * scale)
         np.testing.assert_allclose(lr[off + 3:off + 5], R @ ld[off + 3:off + 5], atol=1e-8 * scale)
         assert abs(lr[off + 2] - ld[off + 2]) < 1e-8 * scale
+
+
+def _virtual_work_of_pressure(nth, nz, p):
+    """Generalized force of the pressure on the linear tilt, computed independently
+    of the oracle's loads: the virtual displacement of the surface point at axial
+    position z is (1 - z/L) de_1 + (z/L) de_3 along x (likewise e_2, e_4 along y), so
+    G = integral of f . dx/de over the gap with traction f = -p n, n = (cos t, sin t).
+    Nodes: cell centres plus the two boundary lines; numpy's trapezoid along z on
+    those nodes, the periodic trapezoid (a plain sum) around theta."""
+    dth = 2 * math.pi / nth
+    dz = L / nz
+    th = (np.arange(nth) + 0.5) * dth
+    zn = np.concatenate([[0.0], (np.arange(nz) + 0.5) * dz, [L]])
+    P = np.vstack([np.full(nth, PCH), p.reshape(nz, nth), np.full(nth, PCASE)])
+    fx = -P * np.cos(th)[None, :]
+    fy = -P * np.sin(th)[None, :]
+    lo = (1.0 - zn / L)[:, None]
+    hi = (zn / L)[:, None]
+
+    def integ(f):
+        return RK * dth * np.trapezoid(f.sum(axis=1), zn)
+
+    return np.array([integ(fx * lo), integ(fy * lo), integ(fx * hi), integ(fy * hi)])
+
+
+def test_generalized_force_is_the_virtual_work_of_the_pressure():
+    """S19 reading of Eq. 2.11: G = (Fx - My/L, Fy + Mx/L, My/L, -Mx/L) is exactly the
+    virtual work of the linear tilt when the traction has no axial part, as for the
+    pressure.  Pinned against the virtual work integrated directly from the pressure
+    field (no forces or moments involved), on a tilted, eccentric, squeezing piston."""
+    nth, nz = 48, 24
+    st = state((6e-6, -3e-6, 2e-6, 5e-6), (3e-5, 1e-5, -2e-5, 4e-5))
+    p, _ = solve_single(nth, nz, PHYS, tex_default(), st)
+    s, ld = oracle.loads(nth, nz, PHYS, tex_default(), st, p)
+    assert s == oracle.OK
+    G = oracle.generalized_force(L, ld[:6])
+    vw = _virtual_work_of_pressure(nth, nz, p)
+    scale = np.abs(vw).max()
+    assert scale > 1.0
+    np.testing.assert_allclose(G, vw, rtol=0, atol=1e-10 * scale)
+    # components of comparable size, so that a flipped sign could not hide
+    assert np.all(np.abs(vw) > 1e-3 * scale)
+
+
+def test_symmetric_squeeze_loads_both_ends_equally():
+    """Parallel squeeze of a concentric piston (edot_1 = edot_3): the pressure mode is
+    symmetric about mid-gap, so the generalized force splits Fx evenly between the two
+    ends, G_1 = G_3 = Fx / 2, and nothing acts along y."""
+    a = 1e-4
+    st = state((0, 0, 0, 0), (a, 0, a, 0))
+    nth, nz = 64, 32
+    p, _ = solve_single(nth, nz, PHYS, SMOOTH, st, eps=1e-13)
+    s, ld = oracle.loads(nth, nz, PHYS, SMOOTH, st, p)
+    F = ld[:6] + ld[6:]
+    G = oracle.generalized_force(L, F)
+    assert abs(G[0] - 0.5 * F[0]) <= 1e-6 * abs(F[0])
+    assert abs(G[2] - 0.5 * F[0]) <= 1e-6 * abs(F[0])
+    assert abs(G[1]) <= 1e-9 * abs(F[0]) and abs(G[3]) <= 1e-9 * abs(F[0])
 
 
 # ----------------------------------------------------------------------------- Jacobian and Picard
