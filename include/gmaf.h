@@ -49,6 +49,7 @@ extern "C" {
 #define GMAF_OUT_OF_MEMORY  -5  /* workspace would exceed the context's HBM budget    */
 #define GMAF_CUDA_ERROR     -6  /* CUDA runtime error; destroy the context            */
 #define GMAF_TIMEOUT        -7  /* a device-side bounded loop gave up                 */
+#define GMAF_CANCELLED      -8  /* a served request was cancelled before it finished  */
 
 /* ---- problem description (Sec. 2.1, Eq. 2.3, Table 8) ---------------- */
 
@@ -241,16 +242,26 @@ int gmaf_phase_timing(const gmaf_ctx *ctx, double ms_out[4], int64_t launches_ou
  * (opts->precision and opts->criterion must be 0), with the
  * same arguments minus the context and plus the stream, and allocates nothing:
  * its scratch is a fixed array of GMAF_NOALLOC_SCRATCH_BYTES inside the
- * library, which every GPU that loads the library holds until the process
- * exits.  A problem needs 1048576 + 7 * ceil256(8 * n_cond * n_theta * n_z)
+ * library.  The array sits in a code module of its own, which CUDA loads on a
+ * device at the first call of this entry point there (lazy module loading, the
+ * default; under CUDA_MODULE_LOADING=EAGER at context creation): that is when
+ * the array's device memory is committed, and the device holds it until the
+ * process exits.  Loading the module can itself fail for lack of memory, so a
+ * caller whose pool allocator later takes the GPU's memory should make one
+ * warm-up call on each device first (it may be a small problem), and make it
+ * before any stream capture: the first call on a device also looks up the
+ * array's device address with that device current.  The array lies outside
+ * every context's hbm_budget_bytes and gmaf_workspace_bytes and outside the
+ * server's footprint admission; the other entry points never load it.
+ * A problem needs 1048576 + 7 * ceil256(8 * n_cond * n_theta * n_z)
  * bytes of it, so at most 1,778,816 joint unknowns (the 9-condition
  * 512 x 256 batch fits);
- * larger problems return GMAF_OUT_OF_MEMORY before any work is issued.
- * The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call
- * uses the same array and leaves its contents behind, so calls whose GPU work
- * overlaps (different streams, threads or processes sharing the library on one
- * device) race on it: serialise them.  Synchronises the stream. */
+ * larger problems return GMAF_OUT_OF_MEMORY before any work is issued.  Every
+ * call uses the same array and leaves its contents behind, so calls whose GPU
+ * work overlaps (different streams, threads or processes sharing the library on
+ * one device) race on it: serialise them.  Synchronises the stream, also when it
+ * returns an error after issuing work, so a failed call leaves nothing running
+ * on the array. */
 #define GMAF_NOALLOC_SCRATCH_BYTES (96u * 1024u * 1024u)
 int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, const double *D,
                              const double *aE, const double *aN, const double *S, double *p,
@@ -312,6 +323,13 @@ int gmaf_server_run(gmaf_server *server, int32_t iterations, int32_t *active_out
 int gmaf_server_poll(gmaf_server *server, gmaf_result *out, int32_t max_results, int32_t *n_out);
 /* Free bytes left in the server's arena. */
 int gmaf_server_free_bytes(const gmaf_server *server, size_t *bytes_out);
+/* Cancel request `id`, queued or admitted: it leaves the queue or the batched set,
+ * its arena block is released at once (after the server's stream has finished
+ * the work already issued for it), and gmaf_server_poll later returns one result
+ * for it with status GMAF_CANCELLED and its input state.  GMAF_INVALID_ARG if
+ * no queued or active request has this id (e.g. it already finished).
+ * Synchronises the server's stream when the request was admitted. */
+int gmaf_server_cancel(gmaf_server *server, int64_t id);
 
 /* Copy the pressure fields of the last Picard step on this context
  * (condition-major, device memory p_out of 9 * n_z * n_theta doubles): the 9

@@ -33,12 +33,15 @@ OK, INVALID, CONTACT, NOT_CONVERGED, NONFINITE, NOMEM = 0, -1, -2, -3, -4, -5
 
 
 def build(force: bool = False) -> str:
-    """Compile gmaf_oracle.c into liboracle.so next to it (seconds)."""
+    """Compile gmaf_oracle.c into liboracle.so next to it (seconds).  OpenMP is used
+    when the compiler has it; without it every loop runs on one thread (same results)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base[:5] + ["-fopenmp"] + base[5:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -53,6 +56,10 @@ def lib():
         if _lib is None:
             build()
             L = ctypes.CDLL(_LIB)
+            L.oracle_set_threads.restype = ctypes.c_int
+            L.oracle_set_threads.argtypes = [ctypes.c_int]
+            L.oracle_max_threads.restype = ctypes.c_int
+            L.oracle_max_threads.argtypes = []
             L.oracle_film.restype = ctypes.c_double
             L.oracle_film.argtypes = [_D, _D, _D, ctypes.c_double, ctypes.c_double]
             L.oracle_film_rate.restype = ctypes.c_double
@@ -92,6 +99,17 @@ def lib():
                                                          _I])
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's independent-iteration loops (n < 1: all processors).
+    Reductions stay sequential, so results do not depend on n.  Returns the count in
+    effect (1 when the library was built without OpenMP)."""
+    return int(lib().oracle_set_threads(int(n)))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
 
 
 def _p(a):

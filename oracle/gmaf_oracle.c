@@ -19,9 +19,16 @@
  * numeric example of the paper, which prints none: the whole path is parity
  * unpinned against the paper's own numbers.
  *
- * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so gmaf_oracle.c -lm
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared -o liboracle.so gmaf_oracle.c -lm
  * (-ffp-contract=off: no fused multiply-add, so x86-64 and aarch64 give the
- * same bits.)
+ * same bits.  -fopenmp is optional: without it every loop runs on one thread.)
+ *
+ * Threads: one by default.  oracle_set_threads(n) lets the loops whose
+ * iterations are independent (assembly per cell, sparse products per row,
+ * element-wise vector updates, the preconditioner's passes) run on n threads.
+ * Each output element is computed by the same arithmetic whichever thread runs
+ * it, and every reduction (dot products, norms, load integrals) stays a plain
+ * sequential loop, so the results are bitwise the same for any thread count.
  *
  * Parameter arrays (plain doubles, so the oracle has no struct in common with
  * the CUDA library):
@@ -40,11 +47,40 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_PI 3.14159265358979323846
 
 enum { OR_OK = 0, OR_INVALID = -1, OR_CONTACT = -2, OR_NOT_CONVERGED = -3,
        OR_NONFINITE = -4, OR_NOMEM = -5 };
+
+/* Threads of the independent-iteration loops (see the header). */
+static int g_threads = 1;
+#define OR_PAR_MIN 8192   /* loops shorter than this stay on one thread */
+
+/* Set the thread count (n < 1: all processors); returns the count in effect. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n >= 1 ? n : omp_get_num_procs();
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+/* Processors available to the loops (1 when built without OpenMP). */
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Texture (Eq. 2.3 h_Text; Fig. 10 is missing from the text, so the layout  */
@@ -201,6 +237,7 @@ int oracle_assemble(int nth, int nz, const double *phys, const double *tex,
     double *aB = (double *)calloc(n, sizeof(double));
     if (!aB) return OR_NOMEM;
 
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(| : contact) if (n >= OR_PAR_MIN)
     for (int j = 0; j < nz; ++j) {
         for (int i = 0; i < nth; ++i) {
             size_t P = (size_t)i + (size_t)nth * (size_t)j;
@@ -234,6 +271,7 @@ int oracle_assemble(int nth, int nz, const double *phys, const double *tex,
             S[P] = -(Ub / 2.0) * (hn - hs) * dx - hdot * dx * dz + sb;
         }
     }
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (n >= OR_PAR_MIN)
     for (int j = 0; j < nz; ++j) {
         for (int i = 0; i < nth; ++i) {
             size_t P = (size_t)i + (size_t)nth * (size_t)j;
@@ -299,6 +337,7 @@ static int csr_build(int nth, int nz, const double *D, const double *aE,
 /* y = A x (part 0 = whole row, part -1 = strictly lower, part +1 = strictly upper) */
 static void csr_apply(const csr *m, int part, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (m->n >= OR_PAR_MIN)
     for (size_t r = 0; r < m->n; ++r) {
         double s = 0.0;
         for (size_t k = m->rowptr[r]; k < m->rowptr[r + 1]; ++k) {
@@ -387,6 +426,7 @@ static void joint_precond(const joint *J, int precond, double omega,
     size_t N = J->n * (size_t)J->ncond;
     const double *D = J->D;
     if (precond == 0) {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
         for (size_t k = 0; k < N; ++k) z[k] = r[k] / D[k];
         return;
     }
@@ -394,6 +434,7 @@ static void joint_precond(const joint *J, int precond, double omega,
         for (int c = 0; c < J->ncond; ++c) {
             const csr *m = &J->blk[c];
             size_t o = (size_t)c * J->n;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (m->n >= OR_PAR_MIN)
             for (size_t row = 0; row < m->n; ++row) {
                 double s = 0.0;
                 for (size_t k = m->rowptr[row]; k < m->rowptr[row + 1]; ++k) {
@@ -408,13 +449,16 @@ static void joint_precond(const joint *J, int precond, double omega,
         return;
     }
     /* t1 = D^-1 r */
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
     for (size_t k = 0; k < N; ++k) t1[k] = r[k] / D[k];
     /* t2 = L t1 ; v = t1 - w D^-1 t2  (stored in t1's place via z) */
     joint_apply(J, -1, t1, t2);
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
     for (size_t k = 0; k < N; ++k) z[k] = t1[k] - omega * (t2[k] / D[k]);
     /* t2 = L^T v ; z = (2-w) w (v - w D^-1 t2) */
     joint_apply(J, +1, z, t2);
     double c = (2.0 - omega) * omega;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
     for (size_t k = 0; k < N; ++k) z[k] = c * (z[k] - omega * (t2[k] / D[k]));
 }
 
@@ -504,6 +548,7 @@ int oracle_solve_joint(int nth, int nz, int ncond, const double *D,
     for (;;) {
         /* step 1-2: r0 = S - A p0, z0 = M^-1 r0, u0 = z0, d0 = r0.z0 */
         joint_apply(&J, 0, p, v);
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
         for (size_t k = 0; k < N; ++k) r[k] = S[k] - v[k];
         rel = sqrt(dot(N, r, r)) / normS;
         int converged = rel <= eps;
@@ -519,7 +564,9 @@ int oracle_solve_joint(int nth, int nz, int ncond, const double *D,
                 if (!isfinite(uv) || !isfinite(d) || !(uv > 0.0)) { st = OR_NONFINITE; goto done; }
                 double alpha = d / uv;
                 /* step 4-5 */
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
                 for (size_t k = 0; k < N; ++k) p[k] = p[k] + alpha * u[k];
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
                 for (size_t k = 0; k < N; ++k) r[k] = r[k] - alpha * v[k];
                 ++iters;
                 /* step 6: synchronized criterion, Eq. 3.9 */
@@ -531,11 +578,13 @@ int oracle_solve_joint(int nth, int nz, int ncond, const double *D,
                 double dn = dot(N, r, z);
                 double beta = dn / d;
                 d = dn;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
                 for (size_t k = 0; k < N; ++k) u[k] = z[k] + beta * u[k];
             }
         }
         /* true residual */
         joint_apply(&J, 0, p, v);
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (N >= OR_PAR_MIN)
         for (size_t k = 0; k < N; ++k) t1[k] = S[k] - v[k];
         true_rel = sqrt(dot(N, t1, t1)) / normS;
         if (!isfinite(true_rel)) { st = OR_NONFINITE; goto done; }

@@ -107,6 +107,7 @@ const char *gmaf_status_string(int st)
     case GMAF_OUT_OF_MEMORY: return "workspace exceeds the HBM budget";
     case GMAF_CUDA_ERROR: return "CUDA runtime error";
     case GMAF_TIMEOUT: return "device-side loop guard expired";
+    case GMAF_CANCELLED: return "request cancelled";
     default: return "unknown status";
     }
 }
@@ -153,6 +154,11 @@ int gmaf_create(gmaf_ctx **out, size_t hbm_budget_bytes, void *cuda_stream)
     const char *rdl = std::getenv("GMAF_RELIABLE_DELTA");
     c->reliable_delta = rdl ? std::atof(rdl) : 0.1;
     if (!(c->reliable_delta > 0.0 && c->reliable_delta < 0.5)) c->reliable_delta = 0.1;
+    // fault injection from the host: a fixed, lower limit for the device loop guard,
+    // so that a test can make it expire (GMAF_TIMEOUT) without any device fault
+    const char *lg = std::getenv("GMAF_LOOP_GUARD");
+    c->loop_guard = lg ? std::atoi(lg) : 0;
+    if (c->loop_guard < 0) c->loop_guard = 0;
     *out = c;
     return GMAF_OK;
 }

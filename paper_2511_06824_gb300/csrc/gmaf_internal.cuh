@@ -68,6 +68,7 @@ struct PcgDesc {
     T omega;                       // ASSOR relaxation factor
     double eps;
     int max_iter;
+    int guard_limit;               // phase-A bodies allowed before GMAF_TIMEOUT (0: max_iter + 4)
     cudaGraphConditionalHandle cond;
     Scalars *sc;
     double *partials;              // per-task (or per-warp) sums [ntiles][2], or per-block [2][grid]
@@ -151,6 +152,7 @@ struct gmaf_ctx {
     double inner_floor;            // smallest relative residual asked of an inner FP32 solve
     int mixed_restart;             // restart the inner FP32 PCG at each refinement (else continue it)
     double reliable_delta;         // continued recurrence: residual reduction between two refinements
+    int loop_guard;                // GMAF_LOOP_GUARD: fixed loop-guard limit (0: max_iter + 4)
 };
 
 namespace gmaf {

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
         publish_task<2>(val, m.partials, t, lane);
         double tot[2];
         if (group_complete<2>(m, g, t, lane, tot) && lane == 0 && !done)   // active all launch
-            finish_b<false>(d.sc, tot[0], tot[1], k, d.eps, d.max_iter);
+            finish_b<false>(d.sc, tot[0], tot[1], k, d.eps, d.max_iter, d.guard_limit);
     }
     if (!last_block(&m.msc->ticket[kTicketB])) return;
     // every group has been completed (and updated) by now

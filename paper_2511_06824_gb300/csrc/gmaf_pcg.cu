@@ -24,70 +24,19 @@
 // dot products are accumulated exactly per thread in two-float form and reduced in
 // FP64).
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "gmaf_internal.cuh"
 #include "gmaf_pcg_kernels.cuh"
+#include "gmaf_pcg_host.cuh"
 #include "gmaf_mphase_kernels.cuh"
 
 namespace gmaf {
 
 // ------------------------------------------------------------------ host driver
-
-static int grid_for(const void *kernel, long long work_items, int num_sms, size_t smem = 0)
-{
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    long long g = (long long)per_sm * num_sms;
-    if (g > work_items) g = work_items;
-    if (g < 1) g = 1;
-    return (int)g;
-}
-
-static int stream_grid(long long N, int num_sms)
-{
-    long long g = (N + kThreads - 1) / kThreads;
-    const long long cap = (long long)num_sms * 8;
-    if (g > cap) g = cap;
-    if (g < 1) g = 1;
-    return (int)g;
-}
-
-#define GMAF_TRY(x)                                  \
-    do {                                             \
-        int st__ = (x);                              \
-        if (st__ != GMAF_OK) return st__;            \
-    } while (0)
-
-#define GMAF_CUDA(x) GMAF_TRY(cuda_status(x))
-
-// The phase kernels of one run: strip width W = 32 * VEC, TY rows per task,
-// MINB blocks per SM requested from the register allocator, and the schedule
-// (0: dynamic tasks; 1: static ranges, phase A marching against phase B).
-template <typename T>
-struct KernelSet {
-    const void *a, *b, *b_init;
-    int W, TY, id;
-    size_t smem_b;             // dynamic shared memory of the phase-B kernels
-    int sched;
-    size_t smem_a;             // dynamic shared memory of the phase-A kernel
-    int p_period;              // iterations between two p updates of phase A (1 or 2)
-};
-
-// id = 1000 VEC + 10 TY + MINB (dynamic), 1000000 + 1000 VEC + MINB (static).
-template <typename T, int VEC, int TY, int MINB, int SCHED = 0>
-static KernelSet<T> ks_of(int)
-{
-    return {(const void *)k_phase_a<T, VEC, TY, MINB, SCHED>,
-            (const void *)k_phase_b<T, VEC, TY, MINB, false, SCHED>,
-            (const void *)k_phase_b<T, VEC, TY, MINB, true, SCHED>, 32 * VEC, TY,
-            SCHED ? 1000000 + 1000 * VEC + MINB : 1000 * VEC + 10 * TY + MINB, 0, SCHED};
-}
 
 // Phase B staged through shared memory D rows ahead (cp.async); id + 100000 D.
 template <typename T, int VEC, int TY, int MINB, int D>
@@ -161,32 +110,11 @@ static int variants(KernelSet<double> *out, bool vec_ok, bool = false)
     return n;
 }
 
-static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
-
-template <typename T>
-static bool vec_ok(const PcgDesc<T> &h)
-{
-    constexpr int V = sizeof(T) == 4 ? 4 : 2;
-    bool ok = (h.nth % V) == 0;
-    const void *ptrs[] = {h.D, h.invD, h.aE, h.aN, h.p, h.z, h.v, h.u[0], h.u[1], h.r[0], h.r[1]};
-    for (const void *q : ptrs) ok = ok && aligned16(q);
-    return ok;
-}
-
 // VEC = 8 float kernels: two 16-byte chunks per lane, n_theta % 8 == 0.
 template <typename T>
 static bool vec8_ok(const PcgDesc<T> &h)
 {
     return sizeof(T) == 4 && vec_ok(h) && (h.nth % 8) == 0;
-}
-
-// Default choice without tuning: the first candidate.
-template <typename T>
-static KernelSet<T> choose_kernels(const PcgDesc<T> &h)
-{
-    KernelSet<T> c[kMaxVariants];
-    variants(c, vec_ok(h), vec8_ok(h));
-    return c[0];
 }
 
 template <typename T>
@@ -196,14 +124,6 @@ struct PcgRun {
     KernelSet<T> ks;
     int grid_a, grid_b, grid_s;
 };
-
-template <typename T>
-static cudaError_t launch(const void *fn, int grid, const PcgDesc<T> *dd, cudaStream_t s,
-                         size_t smem = 0)
-{
-    void *args[] = {(void *)&dd};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
-}
 
 static bool graph_matches(const GraphCache &gc, int ga, int gb, int gs, const void *desc,
                           const void *ka, const void *kb, int pairs)
@@ -286,13 +206,6 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
     gc.pairs = pairs;
     (void)s;
     return GMAF_OK;
-}
-
-// Blocks for a persistent phase kernel: enough to hold every task's warp, at
-// most what stays resident.
-static int phase_grid(const void *kernel, long long ntasks, int num_sms, size_t smem = 0)
-{
-    return grid_for(kernel, (ntasks + kWarps - 1) / kWarps, num_sms, smem);
 }
 
 template <typename T>
@@ -497,19 +410,27 @@ struct PhaseClock {
         cudaEventRecord(ctx->ev[2 * used + 1], s);
         kinds[used++] = kind;
     }
-    // after the stream has been synchronised
-    void collect()
+    // After the stream has been synchronised.  Only the first `real_pairs` phase A
+    // and phase B launches of the chunk ran an iteration; the ones issued after the
+    // run was done returned at once and are not counted.
+    void collect(long long real_pairs)
     {
+        long long seen[2] = {0, 0};
         for (int q = 0; q < used; ++q) {
+            const int k = kinds[q];
+            if (k < 2 && seen[k]++ >= real_pairs) continue;
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]) == cudaSuccess) {
-                ctx->phase_ms[kinds[q]] += ms;
-                ctx->phase_count[kinds[q]] += 1;
+                ctx->phase_ms[k] += ms;
+                ctx->phase_count[k] += 1;
             }
         }
         used = 0;
     }
 };
+
+static_assert(offsetof(Scalars, done) == offsetof(Scalars, iter) + 2 * sizeof(int),
+              "iter, first and done are read back together");
 
 // [reset] [init_r] [init B] WHILE{A, B} [finalize], all on the stream.
 template <typename T>
@@ -533,17 +454,20 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
     if (run.h.use_cond) return GMAF_CUDA_ERROR;
     // host-chunked loop control: phases return at once after `done` is set
     const PcgDesc<T> *dd = run.d_desc;
-    int *done_h = (int *)ctx->pinned;
+    int *it_h = (int *)ctx->pinned;        // iter, first, done of the scalars
     PhaseClock clk{ctx};
     clk.begin(s);
     GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s, run.ks.smem_b));
     clk.end(s, 2);
     const int chunk = 16;
+    int prev_iter = -1;
     for (int it = 0; it <= run.h.max_iter + chunk; it += chunk) {
-        GMAF_CUDA(cudaMemcpyAsync(done_h, &run.h.sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GMAF_CUDA(cudaMemcpyAsync(it_h, &run.h.sc->iter, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
         GMAF_CUDA(cudaStreamSynchronize(s));
-        clk.collect();
-        if (*done_h) break;
+        // every iteration that ran advanced iter by one (phase B's last block)
+        clk.collect(prev_iter < 0 ? 0 : it_h[0] - prev_iter);
+        prev_iter = it_h[0];
+        if (it_h[2]) break;
         for (int q = 0; q < chunk; ++q) {
             clk.begin(s);
             GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s, run.ks.smem_a));
@@ -564,60 +488,6 @@ static int read_scalars(gmaf_ctx *ctx, const Scalars *d_sc, Scalars *h_sc)
     return GMAF_OK;
 }
 
-// ---------------------------------------------------------------- ASSOR-I
-//
-// Eq. 3.2: {M^-1}_ii = w (2 - w) / {(D + w L) D^-1 (D + w L)^T}_ii
-//                    = w (2 - w) / (D_i + w^2 sum_{k in low(i)} a_ik^2 / D_k),
-// low(i) = {S; W if i > 0; E across the wrap if i = n_theta - 1}, the strictly
-// lower couplings in the joint index order.  The PCG phases apply it as a
-// diagonal, through the Jacobi path.  With outer given the result is for the
-// FP32 matrix scale * A (outer->scale, set by k_to_f32), i.e. divided by scale.
-template <typename T>
-static __global__ void __launch_bounds__(kThreads)
-k_assor1_diag(const double *__restrict__ D, const double *__restrict__ aE,
-              const double *__restrict__ aN, int nth, int nz, long long m, double omega,
-              const Scalars *__restrict__ outer, T *__restrict__ out)
-{
-    const long long n = (long long)nth * nz;
-    const double scale = outer ? outer->scale : 1.0;
-    const double c1 = omega * (2.0 - omega), w2 = omega * omega;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
-         q += (long long)gridDim.x * blockDim.x) {
-        const long long P = q % n;
-        const int j = (int)(P / nth), i = (int)(P - (long long)j * nth);
-        double s = 0.0;
-        if (j > 0) {
-            const double a = aN[q - nth];
-            s += a * a / D[q - nth];
-        }
-        if (i > 0) {
-            const double a = aE[q - 1];
-            s += a * a / D[q - 1];
-        }
-        if (i == nth - 1) {
-            const double a = aE[q];
-            s += a * a / D[q - (nth - 1)];
-        }
-        out[q] = (T)(c1 / (D[q] + w2 * s) / scale);
-    }
-}
-
-// The diagonal the PCG phases divide by: 1/D (Jacobi, ASSOR-II) or ASSOR-I's.
-static void diag_inverse64(const gmaf_solver_opts *opts, const double *D, const double *aE,
-                           const double *aN, int nth, int nz, long long m, double *out, int num_sms,
-                           cudaStream_t s)
-{
-    if (opts->precond == 2)
-        k_assor1_diag<double><<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, aE, aN, nth, nz, m,
-                                                                          opts->omega, nullptr, out);
-    else
-        k_invd64<<<stream_grid(m, num_sms), kThreads, 0, s>>>(D, out, m,
-                                                               opts->precond == 1 ? opts->omega : 1.0);
-}
-
-// PCG-kernel preconditioner: ASSOR-II runs its two passes, Jacobi and ASSOR-I
-// divide by the stored diagonal.
-static int kernel_precond(const gmaf_solver_opts *opts) { return opts->precond == 1 ? 1 : 0; }
 
 // ---------------------------------------------------------------- asynchronized criterion
 //
@@ -704,6 +574,7 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
         h.eps = opts->eps;
         h.max_iter = opts->max_iter;
         h.sc = gsc + k;
+        h.guard_limit = ctx->loop_guard;
         h.partials = partials;
         ResidDesc &q = rd[k];
         q = ResidDesc{};
@@ -917,6 +788,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         h.eps = opts->eps;
         h.max_iter = opts->max_iter;
         h.sc = dsc;
+        h.guard_limit = ctx->loop_guard;
         GMAF_TRY(setup_run<double>(ctx, run, (PcgDesc<double> *)dbase));
         GMAF_TRY(prepare<double>(ctx, run, ctx->graph64));
         rd.partials = h.partials;
@@ -936,7 +808,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
                 clk.end(s, 3);
                 GMAF_CUDA(cudaGetLastError());
                 GMAF_TRY(read_scalars(ctx, dsc_outer, ho));
-                clk.collect();
+                clk.collect(0);
             }
             double true_rel = ho->true_rel;
             if (hsc->zero_rhs) {
@@ -1046,7 +918,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
             clk.end(s, 3);
             GMAF_CUDA(cudaGetLastError());
             GMAF_TRY(read_scalars(ctx, dsc_outer, ho));
-            clk.collect();
+            clk.collect(0);
         }
         inf.true_rel_residual = ho->true_rel;
         inf.rel_residual = ho->true_rel;
@@ -1080,6 +952,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
         const int left = opts->max_iter - total_inner;
         const int cap = std::max(1000, 4 * longest);
         h.max_iter = cont ? last_iter + std::min(left, cap) : left;
+        h.guard_limit = ctx->loop_guard;
         GMAF_TRY(prepare<float>(ctx, run, ctx->graph32));
         GMAF_TRY(pcg_once<float>(ctx, run, ctx->graph32, cont, true, cont ? rnorm_prev / ho->rnorm : 0.0));
         rnorm_prev = ho->rnorm;
@@ -1109,220 +982,3 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
 }
 
 }  // namespace gmaf
-
-// ------------------------------------------------------------------ allocation-free joint solve
-//
-// gmaf_solve_joint_noalloc: the FP64 joint solve for callers that may not
-// allocate device memory.  All of its scratch (descriptor, scalars, partial
-// sums, 1/D and the six PCG vectors) lives in one file-scope device array of
-// GMAF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
-// process exits.  Host code cannot use the array's name as a device address, so
-// the address is looked up once per device with cudaGetSymbolAddress and passed
-// to the kernels.  The loop is driven from the host in chunks (no graph, no
-// events, no pinned staging), so nothing here allocates.
-
-namespace gmaf {
-
-static __device__ __align__(256) unsigned char g_noalloc_scratch[GMAF_NOALLOC_SCRATCH_BYTES];
-
-namespace {
-constexpr size_t kNaDesc = 0;          // PcgDesc<double>
-constexpr size_t kNaResid = 2048;      // ResidDesc
-constexpr size_t kNaScal = 4096;       // Scalars of the run, Scalars of the residual
-constexpr size_t kNaCslot = 8192;      // int[kMaxCond], identity coefficient map
-constexpr size_t kNaPart = 16384;      // per-task / per-block partial sums
-constexpr size_t kNaPartBytes = 524288;
-constexpr size_t kNaVec = 1048576;     // 1/D, r0, r1, u0, u1, z, v: N doubles each
-constexpr int kNaMaxDevices = 64;
-static_assert(sizeof(PcgDesc<double>) <= kNaResid - kNaDesc, "descriptor slot");
-static_assert(sizeof(ResidDesc) <= kNaScal - kNaResid, "residual descriptor slot");
-static_assert(2 * sizeof(Scalars) <= kNaCslot - kNaScal, "scalar slot");
-static_assert(kNaPart + kNaPartBytes <= kNaVec, "partials slot");
-
-std::mutex g_na_mutex;
-void *g_na_base[kNaMaxDevices];
-
-size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
-
-// Device address of the scratch array on the current device (looked up once per device).
-int noalloc_base(char **out)
-{
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (dev < 0 || dev >= kNaMaxDevices) return GMAF_CUDA_ERROR;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_base[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || ptr == nullptr) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
-        g_na_base[dev] = ptr;
-    }
-    *out = (char *)g_na_base[dev];
-    return GMAF_OK;
-}
-}  // namespace
-
-}  // namespace gmaf
-
-extern "C" int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, const double *D,
-                                        const double *aE, const double *aN, const double *S,
-                                        double *p, const gmaf_solver_opts *opts,
-                                        void *cuda_stream, int32_t *iters_out,
-                                        double *rel_res_out)
-{
-    using namespace gmaf;
-    if (!grid || !D || !aE || !aN || !S || !p) return GMAF_INVALID_ARG;
-    if (grid->n_theta < 3 || grid->n_z < 2 || n_cond < 1 || n_cond > kMaxCond) return GMAF_INVALID_ARG;
-    if (!opts_valid(opts) || opts->precision != 0 || opts->criterion != 0) return GMAF_INVALID_ARG;
-    const int nth = grid->n_theta, nz = grid->n_z, K = n_cond;
-    const long long n = (long long)nth * nz;
-    const long long N = n * K;
-    const size_t vec = round256((size_t)N * sizeof(double));
-    if ((long long)nth * nz > (1LL << 31) - 1 || kNaVec + 7 * vec > (size_t)GMAF_NOALLOC_SCRATCH_BYTES)
-        return GMAF_OUT_OF_MEMORY;
-    char *base = nullptr;
-    int st = noalloc_base(&base);
-    if (st != GMAF_OK) return st;
-    int dev = 0, num_sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-
-    PcgDesc<double> h{};
-    h.nth = nth;
-    h.nz = nz;
-    h.K = K;
-    h.n = n;
-    h.precond = kernel_precond(opts);
-    h.zero_init = opts->zero_init;
-    h.use_cond = 0;
-    double *vbase = (double *)(base + kNaVec);
-    double *invD = vbase;
-    double *vecs[6];
-    for (int q = 0; q < 6; ++q) vecs[q] = (double *)(base + kNaVec + (size_t)(q + 1) * vec);
-    Scalars *dsc = (Scalars *)(base + kNaScal);
-    Scalars *dsc_res = dsc + 1;
-    int *cslot = (int *)(base + kNaCslot);
-    h.D = D;
-    h.invD = invD;
-    h.aE = aE;
-    h.aN = aN;
-    h.cslot = cslot;
-    h.b = S;
-    h.p = p;
-    h.r[0] = vecs[0];
-    h.r[1] = vecs[1];
-    h.u[0] = vecs[2];
-    h.u[1] = vecs[3];
-    h.z = vecs[4];
-    h.v = vecs[5];
-    h.omega = opts->omega;
-    h.eps = opts->eps;
-    h.max_iter = opts->max_iter;
-    h.sc = dsc;
-    h.partials = (double *)(base + kNaPart);
-    const KernelSet<double> ks = choose_kernels<double>(h);
-    h.tiles_x = (nth + ks.W - 1) / ks.W;
-    h.tiles_y = (nz + ks.TY - 1) / ks.TY;
-    h.ntiles = (long long)h.tiles_x * h.tiles_y * K;
-    const int grid_a = phase_grid(ks.a, h.ntiles, num_sms, ks.smem_a);
-    const int grid_b = phase_grid(ks.b, h.ntiles, num_sms, ks.smem_b);
-    const int grid_s = stream_grid(N, num_sms);
-    long long np = 2 * h.ntiles;
-    if (2LL * grid_s > np) np = 2LL * grid_s;
-    if ((size_t)np * sizeof(double) > kNaPartBytes) return GMAF_OUT_OF_MEMORY;
-    PcgDesc<double> *d_desc = (PcgDesc<double> *)(base + kNaDesc);
-    ResidDesc *d_rdesc = (ResidDesc *)(base + kNaResid);
-    ResidDesc rd{};
-    rd.nth = nth;
-    rd.nz = nz;
-    rd.K = K;
-    rd.n = n;
-    rd.D = D;
-    rd.aE = aE;
-    rd.aN = aN;
-    rd.cslot = cslot;
-    rd.S = S;
-    rd.p = p;
-    rd.sc = dsc_res;
-    rd.partials = h.partials;
-    int slots[kMaxCond];
-    for (int k = 0; k < K; ++k) slots[k] = k;
-
-    // The array keeps the previous call's contents: clear the scalars and the
-    // reduction tickets, which must start at zero.  The copies below come from
-    // pageable (stack) memory and have consumed their sources when they return.
-    e = cudaMemsetAsync(base + kNaScal, 0, kNaCslot - kNaScal, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(cslot, slots, (size_t)K * sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_desc, &h, sizeof(h), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
-    diag_inverse64(opts, D, aE, aN, nth, nz, N, invD, num_sms, s);
-
-    Scalars hs{}, hr{};
-    int restarted = 0;
-    bool keep = false, init_r = true;
-    int status = GMAF_NOT_CONVERGED;
-    double true_rel = 0.0;
-    for (;;) {
-        k_reset<<<1, 32, 0, s>>>(dsc, keep ? 1 : 0);
-        if (init_r) k_init_r<double><<<grid_s, kThreads, 0, s>>>(d_desc);
-        e = launch<double>(ks.b_init, grid_b, d_desc, s, ks.smem_b);
-        if (e == cudaSuccess) e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_status(e);
-        const int chunk = 16;
-        for (int it = 0; it <= opts->max_iter + chunk; it += chunk) {
-            int done = 0;
-            e = cudaMemcpyAsync(&done, &dsc->done, sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return cuda_status(e);
-            if (done) break;
-            for (int q = 0; q < chunk && e == cudaSuccess; ++q) {
-                e = launch<double>(ks.a, grid_a, d_desc, s, ks.smem_a);
-                if (e == cudaSuccess) e = launch<double>(ks.b, grid_b, d_desc, s, ks.smem_b);
-            }
-            if (e != cudaSuccess) return cuda_status(e);
-        }
-        k_finalize<double><<<grid_s, kThreads, 0, s>>>(d_desc);
-        e = cudaMemcpyAsync(&hs, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_status(e);
-        // true residual S - A p into r[iter & 1], where a restart reads it
-        rd.r = h.r[hs.iter & 1];
-        e = cudaMemcpyAsync(d_rdesc, &rd, sizeof(rd), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_status(e);
-        k_resid64<<<grid_s, kThreads, 0, s>>>(d_rdesc);
-        e = cudaMemcpyAsync(&hr, dsc_res, sizeof(Scalars), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_status(e);
-        true_rel = hr.true_rel;
-        if (hs.zero_rhs) {
-            e = cudaMemsetAsync(p, 0, (size_t)N * sizeof(double), s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return cuda_status(e);
-            true_rel = 0.0;
-        }
-        if (hs.status != 0 || hr.status != 0) {
-            status = hs.status != 0 ? hs.status : hr.status;
-            break;
-        }
-        if ((hs.converged || hs.zero_rhs) && true_rel <= 10.0 * opts->eps) {
-            status = GMAF_OK;
-            break;
-        }
-        if (restarted || hs.iter >= opts->max_iter) {
-            status = GMAF_NOT_CONVERGED;
-            break;
-        }
-        restarted = 1;
-        keep = true;
-        init_r = false;
-    }
-    if (iters_out) *iters_out = hs.iter;
-    if (rel_res_out) *rel_res_out = true_rel;
-    return status;
-}
-

@@ -845,7 +845,7 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
 // loop guard.  Returns 1 when the run is done.
 template <bool INIT>
 __device__ __forceinline__ int finish_b(Scalars *sc, double rz, double rr, int k, double eps,
-                                        int max_iter)
+                                        int max_iter, int guard_limit)
 {
     const double rel = sqrt(rr) / sc->normS;
     sc->rel = rel;
@@ -892,7 +892,8 @@ __device__ __forceinline__ int finish_b(Scalars *sc, double rz, double rr, int k
             sc->beta = rz / sc->d;
             sc->d = rz;
         }
-        if (sc->guard > max_iter + 4) {   // loop guard: never more bodies than iterations
+        // loop guard: never more bodies than iterations (a host-set limit can lower it)
+        if (sc->guard > (guard_limit > 0 ? guard_limit : max_iter + 4)) {
             sc->status = GMAF_TIMEOUT;
             done = 1;
         }
@@ -951,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__
     double tot[2];
     if (reduce_units<2>(reducer_of(d), ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
         threadIdx.x == 0) {
-        const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter);
+        const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter, d.guard_limit);
         if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
     }
 }
@@ -1629,7 +1630,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc
     double tot[2];
     if (reduce_units<2>(reducer_of(d), ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
         threadIdx.x == 0) {
-        const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter);
+        const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter, d.guard_limit);
         if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
     }
 }

@@ -271,6 +271,7 @@ static int start_inner(gmaf_server *sv, Request *r, double true_rel, double rnor
     const bool cont = continued && r->outer > 0 && !r->stalled && r->rnorm_prev > 0.0;
     const int left = r->in.max_iter - r->total_inner;
     r->h.max_iter = cont ? r->last_iter + std::min(left, std::max(1000, 4 * r->longest)) : left;
+    r->h.guard_limit = sv->ctx->loop_guard;
     cudaError_t e = cudaMemcpyAsync(r->d_desc, &r->h, sizeof(PcgDesc<float>), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
     k_make_b32<<<r->grid_s, kThreads, 0, s>>>(r->r64, r->b32, r->N, r->sc_out);
@@ -749,6 +750,44 @@ int gmaf_server_free_bytes(const gmaf_server *sv, size_t *bytes_out)
 {
     if (!sv || !bytes_out) return GMAF_INVALID_ARG;
     *bytes_out = sv->arena.free_bytes();
+    return GMAF_OK;
+}
+
+int gmaf_server_cancel(gmaf_server *sv, int64_t id)
+{
+    if (!sv) return GMAF_INVALID_ARG;
+    Request *r = nullptr;
+    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+        if ((*it)->id == id) {
+            r = *it;
+            sv->queue.erase(it);
+            break;
+        }
+    }
+    if (!r) {
+        for (auto it = sv->active.begin(); it != sv->active.end(); ++it) {
+            if ((*it)->id == id) {
+                r = *it;
+                // work already issued for it (the next inner solve's set-up) may still
+                // be running on its block: let it finish before the block is reused
+                cudaError_t e = cudaStreamSynchronize(sv->stream);
+                if (e != cudaSuccess) return cuda_status(e);
+                sv->active.erase(it);
+                sv->arena.release(r->off, r->bytes);
+                sv->dirty = true;
+                break;
+            }
+        }
+    }
+    if (!r) return GMAF_INVALID_ARG;
+    gmaf_result out{};
+    out.id = r->id;
+    out.status = GMAF_CANCELLED;
+    out.iterations = r->total_inner;
+    out.outer_iterations = r->outer;
+    out.state = r->in.state;
+    sv->finished.push_back(out);
+    delete r;
     return GMAF_OK;
 }
 

@@ -27,6 +27,7 @@ GMAF_NONFINITE = -4
 GMAF_OUT_OF_MEMORY = -5
 GMAF_CUDA_ERROR = -6
 GMAF_TIMEOUT = -7
+GMAF_CANCELLED = -8
 
 EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_bytes",
             "gmaf_last_solve_info", "gmaf_assemble", "gmaf_solve_joint", "gmaf_integrate_loads",
@@ -34,7 +35,7 @@ EXPORTED = ("gmaf_create", "gmaf_destroy", "gmaf_set_stream", "gmaf_workspace_by
             "gmaf_phase_timing", "gmaf_solve_joint_noalloc", "gmaf_request_footprint",
             "gmaf_server_create", "gmaf_server_destroy", "gmaf_server_submit", "gmaf_server_run",
             "gmaf_server_poll", "gmaf_server_free_bytes", "gmaf_last_fields",
-            "gmaf_picard_step_simplified")
+            "gmaf_picard_step_simplified", "gmaf_server_cancel")
 
 
 class gmaf_grid(ctypes.Structure):
@@ -141,6 +142,7 @@ def load(path: str = LIB_PATH):
     L.gmaf_server_poll.argtypes = [_VP, ctypes.POINTER(gmaf_result), ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_int32)]
     L.gmaf_server_free_bytes.argtypes = [_VP, ctypes.POINTER(ctypes.c_size_t)]
+    L.gmaf_server_cancel.argtypes = [_VP, ctypes.c_int64]
     L.gmaf_last_fields.argtypes = [_VP, ctypes.POINTER(gmaf_grid), _VP]
     L.gmaf_status_string.argtypes = [ctypes.c_int]
     L.gmaf_status_string.restype = ctypes.c_char_p
@@ -264,8 +266,11 @@ def gmaf_assemble(ctx: int, n_theta: int, n_z: int, phys, tex, conds, D, aE, aN,
 
 
 def gmaf_solve_joint(ctx: int, n_theta: int, n_z: int, n_cond: int, D, aE, aN, S, p,
-                     opts: Optional[gmaf_solver_opts] = None, allow_not_converged: bool = False):
-    """Returns (status, iterations, true relative residual)."""
+                     opts: Optional[gmaf_solver_opts] = None, allow_not_converged: bool = False,
+                     allow: Sequence[int] = ()):
+    """Returns (status, iterations, true relative residual).  Statuses other than
+    GMAF_OK (and GMAF_NOT_CONVERGED with allow_not_converged, or any listed in
+    allow) raise GmafError."""
     n = n_cond * n_theta * n_z
     g = grid(n_theta, n_z)
     o = opts or solver_opts()
@@ -276,7 +281,7 @@ def gmaf_solve_joint(ctx: int, n_theta: int, n_z: int, n_cond: int, D, aE, aN, S
                                  _dev(p, n, "p"), ctypes.byref(o), ctypes.byref(it),
                                  ctypes.byref(rel))
     ok = (GMAF_OK, GMAF_NOT_CONVERGED) if allow_not_converged else (GMAF_OK,)
-    _check("gmaf_solve_joint", st, ok)
+    _check("gmaf_solve_joint", st, tuple(ok) + tuple(allow))
     return st, it.value, rel.value
 
 
@@ -442,6 +447,10 @@ class Server:
         _check("gmaf_server_free_bytes", load().gmaf_server_free_bytes(_VP(self.handle),
                                                                         ctypes.byref(b)))
         return b.value
+
+    def cancel(self, request_id: int):
+        _check("gmaf_server_cancel", load().gmaf_server_cancel(_VP(self.handle),
+                                                                int(request_id)))
 
     def close(self):
         if self.handle:

@@ -1,0 +1,148 @@
+"""Failure detection without any GPU fault: every failure is made on the host.
+
+- Non-finite data (a NaN in S, an Inf in D) is only data to the kernels: the
+  reductions see it and the solve returns GMAF_NONFINITE; the context stays usable.
+- A non-finite state is refused before any work (GMAF_INVALID_ARG).
+- The device loop guard is made to expire by lowering its limit from the host
+  (GMAF_LOOP_GUARD, read when a context is created): the solve returns
+  GMAF_TIMEOUT from a bounded device loop, and a context without the limit
+  solves the same system.
+- A served request is cancelled while queued and while admitted: its arena block
+  is released and it yields one GMAF_CANCELLED result; the others are unaffected.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_06824_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = (60.0 / 600.0) / 360.0
+F_EXT = np.array([30.0, -15.0, 6.0, -3.0])
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_06824_gb300 import build, gmaf
+    build.build()
+    gmaf.load()
+    return gmaf
+
+
+def system(nth=96, nz=40, K=3, seed=1):
+    w = inputs.make(f"textured-{nth}x{nz}-k{K}", seed)
+    conds = [inputs.random_state(np.random.default_rng(seed + k)) for k in range(K)]
+    st, D, aE, aN, S = oracle.assemble_joint(nth, nz, w.phys, w.tex, conds)
+    assert st == oracle.OK
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()  # noqa: E731
+    return (nth, nz, K), dev(D), dev(aE), dev(aN), dev(S)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("where", ["nan_in_S", "inf_in_D"])
+def test_nonfinite_input_is_reported_and_the_context_stays_usable(g, precision, where):
+    (nth, nz, K), D, aE, aN, S = system()
+    bad_D, bad_S = D.clone(), S.clone()
+    i = K * nth * nz // 2 + 17
+    if where == "nan_in_S":
+        bad_S[i] = float("nan")
+    else:
+        bad_D[i] = float("inf")
+    opts = g.solver_opts(eps=1e-10, precision=precision)
+    with g.Context() as c:
+        p = torch.zeros_like(S)
+        st, _, _ = g.gmaf_solve_joint(c.handle, nth, nz, K, bad_D, aE, aN, bad_S, p, opts,
+                                      allow=(g.GMAF_NONFINITE,))
+        assert st == g.GMAF_NONFINITE, g.status_string(st)
+        # the same context solves the clean system afterwards, as a fresh one does
+        p1 = torch.zeros_like(S)
+        g.gmaf_solve_joint(c.handle, nth, nz, K, D, aE, aN, S, p1, opts)
+    with g.Context() as c2:
+        p2 = torch.zeros_like(S)
+        g.gmaf_solve_joint(c2.handle, nth, nz, K, D, aE, aN, S, p2, opts)
+    assert torch.equal(p1, p2)
+    assert torch.isfinite(p1).all()
+
+
+def test_nonfinite_state_is_refused_before_any_work(g):
+    w = inputs.make("textured-64x32-k9", 0)
+    st = w.state.copy()
+    st[2] = float("nan")
+    with g.Context() as c:
+        r = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st, w.state[:4], DT,
+                               F_EXT, w.d_e, w.d_edot, g.solver_opts(),
+                               allow=(g.GMAF_INVALID_ARG,))
+        assert r["status"] == g.GMAF_INVALID_ARG
+        assert np.isnan(r["state"][2]) and np.array_equal(r["state"][[0, 1, 3]], st[[0, 1, 3]])
+        ok = g.gmaf_picard_step(c.handle, w.n_theta, w.n_z, w.phys, w.tex, w.state, w.state[:4],
+                                DT, F_EXT, w.d_e, w.d_edot, g.solver_opts())
+        assert ok["status"] == g.GMAF_OK
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_loop_guard_expires_with_a_timeout_status(g, monkeypatch, precision):
+    (nth, nz, K), D, aE, aN, S = system()
+    opts = g.solver_opts(eps=1e-12, precision=precision, max_iter=100000)
+    monkeypatch.setenv("GMAF_LOOP_GUARD", "5")
+    with g.Context() as c:
+        p = torch.zeros_like(S)
+        st, it, _ = g.gmaf_solve_joint(c.handle, nth, nz, K, D, aE, aN, S, p, opts,
+                                       allow=(g.GMAF_TIMEOUT,))
+        assert st == g.GMAF_TIMEOUT, g.status_string(st)
+        info = g.gmaf_last_solve_info(c.handle)
+        assert info["status"] == g.GMAF_TIMEOUT and info["iterations"] <= 8
+    monkeypatch.delenv("GMAF_LOOP_GUARD")
+    with g.Context() as c:
+        p = torch.zeros_like(S)
+        st, it, rel = g.gmaf_solve_joint(c.handle, nth, nz, K, D, aE, aN, S, p, opts)
+        assert st == g.GMAF_OK and it > 8 and rel <= 1e-11
+
+
+def _item(nth, nz, seed):
+    from paper_2511_06824_gb300 import serving
+    rng = np.random.default_rng(seed)
+    return serving.StreamItem(0.0, nth, nz, inputs.phys_vector(), inputs.dimple_texture(rng),
+                              inputs.random_state(rng), F_EXT)
+
+
+def test_cancel_queued_and_admitted_requests(g):
+    from paper_2511_06824_gb300 import serving
+    a, b, c = _item(128, 64, 1), _item(128, 64, 2), _item(64, 32, 3)
+    one = g.gmaf_request_footprint(128, 64)
+    with g.Context() as ctx:
+        # alone: the reference result of c
+        with g.Server(ctx.handle, 4 * one) as sv:
+            ic = sv.submit(serving.to_request(c, 1e-10))
+            ref = []
+            while not ref:
+                sv.run(32)
+                ref = sv.poll()
+        # room for one 128 x 64 request at a time: a is admitted, b and c wait
+        with g.Server(ctx.handle, one + (one >> 1)) as sv:
+            full = sv.free_bytes()
+            ia = sv.submit(serving.to_request(a, 1e-10))
+            ib = sv.submit(serving.to_request(b, 1e-10))
+            ic = sv.submit(serving.to_request(c, 1e-10))
+            active, queued = sv.run(4)
+            assert (active, queued) == (1, 2)
+            assert sv.free_bytes() < full
+            sv.cancel(ib)                       # queued
+            sv.cancel(ia)                       # admitted, mid-solve
+            assert sv.free_bytes() == full
+            with pytest.raises(RuntimeError):
+                sv.cancel(ia)                   # no longer known
+            res = {}
+            while len(res) < 3:
+                sv.run(32)
+                for r in sv.poll():
+                    res[r["id"]] = r
+            assert sv.free_bytes() == full
+    assert res[ia]["status"] == g.GMAF_CANCELLED and res[ib]["status"] == g.GMAF_CANCELLED
+    assert np.array_equal(res[ia]["state"], a.state) and np.array_equal(res[ib]["state"], b.state)
+    assert res[ic]["status"] == g.GMAF_OK
+    for k in ("loads", "J", "G", "state"):
+        assert np.array_equal(res[ic][k], ref[0][k]), k

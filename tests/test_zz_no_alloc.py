@@ -5,10 +5,13 @@ they run: a host application whose own pool allocator owns all of the GPU's
 memory and gives solver plug-ins no allocation hook, or a real-time
 co-simulation loop that cannot accept the latency, or the possible failure, of
 an allocation in the middle of a time step.  gmaf_solve_joint_noalloc serves
-them with a fixed scratch array inside the library.  This test calls it through
-the C ABI twice in a row, on two different problems, and checks each result
-against gmaf_solve_joint (pressure relative L2 1e-9, the FP64 parity bound of
-the other tests); a problem larger than the array must be refused.
+them with a fixed scratch array inside the library.  These tests call it through
+the C ABI several times in a row, on different problems, and check each result
+against gmaf_solve_joint and against the oracle's solve of the same system
+(pressure relative L2 1e-9, the FP64 parity bound of the other tests), up to
+the documented fit of the array (the 9-condition 512 x 256 batch) and with an
+odd n_theta (the one-column kernels); a problem larger than the array must be
+refused.
 
 The file name puts it last in collection order, so that a run stopping at the
 first failure has run every other test before this one.
@@ -64,6 +67,34 @@ def test_noalloc_solve_matches_solve_joint_twice_in_a_row(g):
             assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("nth,nz,K,seed,textured,precond", [
+    (512, 256, 9, 4, False, 1),      # the documented fit: the largest vector offsets
+    (151, 48, 5, 5, True, 1),        # odd n_theta: one column per lane
+    (151, 48, 2, 6, True, 0),        # odd n_theta, Jacobi
+])
+def test_noalloc_solve_matches_the_oracle(g, nth, nz, K, seed, textured, precond):
+    D, aE, aN, S = _problem(nth, nz, K, seed, textured)
+    n = K * nth * nz
+    opts = g.solver_opts(eps=1e-10, precond=precond)
+    p1 = torch.full((n,), -3.0, dtype=torch.float64, device="cuda")
+    st, it, rel = g.gmaf_solve_joint_noalloc(nth, nz, K, D, aE, aN, S, p1, opts)
+    assert st == 0 and rel <= 1e-9
+    # a second call on the same array must not see the first one's leftovers
+    p2 = torch.full((n,), 11.0, dtype=torch.float64, device="cuda")
+    st2, it2, rel2 = g.gmaf_solve_joint_noalloc(nth, nz, K, D, aE, aN, S, p2, opts)
+    assert st2 == 0 and it2 == it and torch.equal(p1, p2)
+    oracle.set_threads(0)
+    try:
+        sto, po, ito, _, trelo = oracle.solve_joint(nth, nz, *(a.cpu().numpy() for a in (D, aE, aN, S)),
+                                                    precond=precond, eps=1e-10)
+    finally:
+        oracle.set_threads(1)
+    assert sto == oracle.OK
+    assert abs(it - ito) <= 2, (it, ito)
+    a, b = p1.cpu().numpy(), po.ravel()
+    assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch(g):
