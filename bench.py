@@ -44,6 +44,7 @@ WORKLOAD = "textured-2048x1024-k9"
 METRIC = "joint ASSOR-PCG DOF*iter/s"
 UNIT = "DOF*iter/s"
 DT = (60.0 / 600.0) / 360.0        # one shaft-angle degree at 600 rpm
+DYN_KAPPA = 0.2                    # synthetic side-load scale of the dynamics mode
 L2_BYTES = 135528448
 
 
@@ -69,6 +70,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=20.0, help="arrival rate [1/s] (serving)")
     ap.add_argument("--budget-gb", type=float, default=24.0, help="server HBM budget (serving)")
     ap.add_argument("--dyn-steps", type=int, default=36, help="shaft-angle steps (dynamics)")
+    ap.add_argument("--kappa", type=float, default=None,
+                    help="scale of the synthetic side load (dynamics; default: the calibrated value)")
+    ap.add_argument("--mass", type=float, default=None,
+                    help="piston mass of the inertia load in kg (dynamics; default m_K of Table 8)")
     ap.add_argument("--scheme", choices=["general", "simplified", "both"], default="general",
                     help="Picard scheme of the march (dynamics): the general double-Jacobian "
                          "one (Eq. 2.12-2.19), the conventional simplified one (Eq. 2.20-2.22), "
@@ -480,19 +485,22 @@ def run_dynamics(args):
     st0 = np.concatenate([w.state[:4] * 0.2, np.zeros(4)])
     prec = 1 if args.precision == "mixed" else 0
     schemes = ["general", "simplified"] if args.scheme == "both" else [args.scheme]
+    kappa = DYN_KAPPA if args.kappa is None else args.kappa
+    mass = dynamics.PISTON_MASS if args.mass is None else args.mass
     runs = {}
     with gmaf.Context() as c:
         for scheme in schemes:
-            dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof, 2,
-                           opts=gmaf.solver_opts(precision=prec), scheme=scheme)   # warm-up
+            dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof, 2, kappa=kappa,
+                           mass=mass, opts=gmaf.solver_opts(precision=prec), scheme=scheme)  # warm-up
             torch.cuda.synchronize()
             recs = []
             t0 = time.perf_counter()
             failure = None
             try:
                 dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof,
-                               args.dyn_steps, opts=gmaf.solver_opts(precision=prec),
-                               on_step=recs.append, scheme=scheme)
+                               args.dyn_steps, kappa=kappa, mass=mass,
+                               opts=gmaf.solver_opts(precision=prec), on_step=recs.append,
+                               scheme=scheme)
             except gmaf.GmafError as ex:
                 failure = {"step": len(recs), "status": ex.status, "message": str(ex)}
             torch.cuda.synchronize()
@@ -508,14 +516,18 @@ def run_dynamics(args):
                 "all_converged": failure is None and all(r.converged for r in recs),
                 "unconverged_steps": sum(not r.converged for r in recs), "failure": failure,
                 "max_e_over_c": float(max((np.abs(r.state[:4]).max() for r in recs), default=0.0)
-                                      / w.phys[2])}
+                                      / w.phys[2]),
+                # the largest |e_i| / c of every tenth of a revolution (36 shaft steps)
+                "e_over_c_per_36_steps": [round(float(max(np.abs(r.state[:4]).max()
+                                                          for r in recs[q:q + 36]) / w.phys[2]), 4)
+                                          for q in range(0, len(recs), 36)]}
     head = runs[schemes[0]]
     out = {"metric": "Picard steps/s (multi-period march)", "value": head["value"],
            "unit": "Picard steps/s", "higher_is_better": True, "n_gpus": 1,
            "shaft_steps": args.dyn_steps, "scheme": schemes[0],
            "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
            "config": {"workload": wl, "joint_dof": w.dof, "steps_per_rev": 360,
-                      "warm_start": True, "kappa": 0.2, "tol_F": 1e-6}}
+                      "warm_start": True, "kappa": kappa, "piston_mass_kg": mass, "tol_F": 1e-6}}
     out.update({k: v for k, v in head.items() if k not in ("value", "unit")})
     if len(schemes) > 1:
         out["schemes"] = runs

@@ -282,7 +282,16 @@ int gmaf_solve_joint_noalloc(const gmaf_grid *grid, int32_t n_cond, const double
  * memory.  Finished results are collected with gmaf_server_poll in completion
  * order.  Each request keeps its own scalars and convergence test
  * (Eq. 3.9 per request), so its result does not depend on which other
- * requests share the GPU.  Not thread-safe. */
+ * requests share the GPU.  Not thread-safe.
+ * Tiling: every request's tasks span 128 columns and a number of rows chosen
+ * per grid by an autotuner: the first request of a grid on a device times one
+ * batched PCG iteration on its own data for each candidate (16, 32, 64 rows) and
+ * the fastest is kept for that grid for the life of the process (so a request's
+ * decomposition, hence its result, depends only on its grid).  Rounds are CUDA
+ * graphs of `iterations` phase pairs, re-instantiated only when the round
+ * length or the kernels change and updated in place when the launch grid does.
+ * Environment (read when a server is created): GMAF_SV_GRAPH=0 drives rounds
+ * from the host instead, GMAF_SV_TUNE=0 keeps 32 rows for every grid. */
 typedef struct gmaf_server gmaf_server;
 
 typedef struct {
@@ -308,6 +317,7 @@ typedef struct {
     double loads[12];          /* base-condition loads: pressure then shear */
     double J[48];              /* 6 x 8 Jacobian, row-major */
     double G[4];               /* generalized force before the update */
+    int32_t tile_rows;         /* rows per task of its batched PCG tasks (tuned per grid) */
 } gmaf_result;
 
 /* Device bytes one request of this grid occupies in a server's arena. */

@@ -69,6 +69,7 @@ struct PcgDesc {
     double eps;
     int max_iter;
     int guard_limit;               // phase-A bodies allowed before GMAF_TIMEOUT (0: max_iter + 4)
+    int ty;                        // rows per task of the batched kernels (0: their template TY)
     cudaGraphConditionalHandle cond;
     Scalars *sc;
     double *partials;              // per-task (or per-warp) sums [ntiles][2], or per-block [2][grid]

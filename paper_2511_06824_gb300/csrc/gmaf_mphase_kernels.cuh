@@ -11,8 +11,8 @@ namespace gmaf {
 // ------------------------------------------------------------------ batched groups
 //
 // Several joint systems ("groups": requests of uneven grids, each with its own
-// scalars, synchronized criterion and buffers) in one persistent launch per CG
-// phase.  Global task t belongs to group g with task_off[g] <= t < task_off[g+1].
+// scalars, synchronized criterion, buffers and task height d.ty) in one
+// persistent launch per CG phase.  Global task t belongs to group g with task_off[g] <= t < task_off[g+1].
 // Groups whose run is done are skipped (a device-side active mask).  Each task
 // publishes its sums at its global index.  The sums of a group are reduced in
 // two levels relative to the group (chunks of kChunk of its tasks, then its
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_a(const MultiDesc<T> 
         beta = __shfl_sync(0xffffffffu, beta, 0);
         double val[1] = {0.0};
         if (!done) {
-            const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
+            const Task tk = task_of_rows<W>(t - m.task_off[g], d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
             if constexpr (D > 0)
                 val[0] = run_task_a_staged<T, VEC, TY, D, PAIR>(d, tk, k, first, pend, (T)alpha,
                                                                 (T)alpha_pp, (T)beta, ring, ub, ab, lane);
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_mphase_b(const MultiDesc<T> 
         alpha = __shfl_sync(0xffffffffu, alpha, 0);
         double val[2] = {0.0, 0.0};
         if (!done) {
-            const Task tk = task_of<W, TY>(t - m.task_off[g], d.K, d.tiles_x, d.nz);
+            const Task tk = task_of_rows<W>(t - m.task_off[g], d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
             if constexpr (D > 0) {
                 // FP64: interior tiles take the body without the periodic-wrap tests
                 if constexpr (sizeof(T) == 8) {

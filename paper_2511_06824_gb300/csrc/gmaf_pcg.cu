@@ -68,10 +68,30 @@ static KernelSet<T> ks_staged_ab()
     return ks;
 }
 
+// Phase A staged DA rows ahead (cp.async) and phase B filled by one lane's bulk
+// copies of whole row segments DB rows ahead (cp.async.bulk + mbarrier);
+// id 2000000 + 200000 DA + 100000 DB + 1000 VEC + 10 TY + MINB.
+template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
+static KernelSet<T> ks_bulk_ab()
+{
+    KernelSet<T> ks = ks_staged_ab<T, VEC, TY, MINB, DA, DB>();
+    const size_t smem = (size_t)kWarps * RingB<T, VEC>::per_warp(DB) * sizeof(T);
+    const void *b = (const void *)k_phase_b_bulk<T, VEC, TY, MINB, false, DB>;
+    const void *bi = (const void *)k_phase_b_bulk<T, VEC, TY, MINB, true, DB>;
+    static std::atomic<unsigned long long> done_b{0}, done_bi{0};
+    smem_optin(done_b, b, smem);
+    smem_optin(done_bi, bi, smem);
+    ks.b = b;
+    ks.b_init = bi;
+    ks.smem_b = smem;
+    ks.id += 2000000;
+    return ks;
+}
+
 constexpr int kMaxVariants = 16;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
-static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
+static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bool bulk_ok = false)
 {
     int n = 0;
     if (vec_ok) {
@@ -79,6 +99,7 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
         // schedule keep every warp busy on smaller ones (1024 x 512 x 9 has only
         // 1152 tasks of 32 rows for 2432 resident warps)
         out[n++] = ks_staged_ab<float, 4, 32, 2, 2>();
+        if (bulk_ok) out[n++] = ks_bulk_ab<float, 4, 32, 2, 2>();
         out[n++] = ks_staged_ab<float, 4, 16, 2, 2>();
         out[n++] = ks_of<float, 4, 32, 2>(0);
         out[n++] = ks_staged<float, 4, 32, 2, 2>();
@@ -95,7 +116,7 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false)
     return n;
 }
 
-static int variants(KernelSet<double> *out, bool vec_ok, bool = false)
+static int variants(KernelSet<double> *out, bool vec_ok, bool = false, bool = false)
 {
     int n = 0;
     if (vec_ok) {
@@ -115,6 +136,14 @@ template <typename T>
 static bool vec8_ok(const PcgDesc<T> &h)
 {
     return sizeof(T) == 4 && vec_ok(h) && (h.nth % 8) == 0;
+}
+
+// Bulk-copied phase B (float, 4 columns a lane): 16-byte row pieces and at most
+// one wrap per row segment of 136 columns.
+template <typename T>
+static bool bulk_ok(const PcgDesc<T> &h)
+{
+    return sizeof(T) == 4 && vec_ok(h) && h.nth >= 32 * 4 + 8;
 }
 
 template <typename T>
@@ -334,7 +363,7 @@ static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
     run.d_desc = desc_slot;
     KernelSet<T> cand[kMaxVariants];
     const bool vo = vec_ok(h);
-    const int ncand = variants(cand, vo, vec8_ok(h));
+    const int ncand = variants(cand, vo, vec8_ok(h), bulk_ok(h));
     int pick = 0;
     TuneEntry key{};
     key.tsize = (int)sizeof(T);
@@ -626,6 +655,7 @@ static int solve_async64(gmaf_ctx *ctx, int nth, int nz, int K, const int *cslot
     const int grid_m = std::min(phase_grid(kma, total, ctx->num_sms),
                                 phase_grid(kmb, total, ctx->num_sms, smem_b));
     void *margs[] = {(void *)&d_m};
+    GMAF_CUDA(cudaMemsetAsync(rsc, 0, (size_t)K * sizeof(Scalars), s));   // clean residual records
     // start: r0 = S_k - A_k p0, z0, d0 and the first criterion test, per condition
     for (int k = 0; k < K; ++k) {
         k_reset<<<1, 32, 0, s>>>(gsc + k, 0);
@@ -723,6 +753,9 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     GMAF_TRY(ensure(ctx, B_SCAL, (3 + 2 * kMaxCond) * sizeof(Scalars)));
     Scalars *dsc = (Scalars *)ctx->buf[B_SCAL];        // PCG run (FP64, or FP32 inner)
     Scalars *dsc_outer = dsc + 1;                       // FP64 residual of the outer loop
+    // the residual kernel only ever raises its status: start every solve from a
+    // clean record, so that a non-finite earlier solve does not leak into this one
+    GMAF_CUDA(cudaMemsetAsync(dsc_outer, 0, sizeof(Scalars), s));
     GMAF_TRY(ensure(ctx, B_CSLOT, kMaxCond * sizeof(int)));
     int *cs_pin = (int *)((char *)ctx->pinned + 6144);
     std::memcpy(cs_pin, cslot_host, (size_t)K * sizeof(int));

@@ -42,6 +42,16 @@ struct Acc<float> {
         hi = s;
         lo = __fadd_rn(lo, __fadd_rn(e, pe));
     }
+    // add(s, 1) without the TwoProduct: s * 1 is exact (error term 0), so this is
+    // bitwise the same as add(s, 1.0f) in fewer instructions
+    __device__ __forceinline__ void add_sum(float p)
+    {
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
@@ -214,7 +224,13 @@ struct Vec<double, 2> {
 template <typename T>
 struct RowAcc {
     Acc<T> acc;
-    __device__ __forceinline__ void add_row(T s) { acc.add(s, T(1)); }
+    __device__ __forceinline__ void add_row(T s)
+    {
+        if constexpr (sizeof(T) == 4)
+            acc.add_sum(s);
+        else
+            acc.add(s, T(1));
+    }
     __device__ __forceinline__ double value() const { return acc.value(); }
 };
 
@@ -233,6 +249,22 @@ __device__ __forceinline__ Task task_of(long long t, int K, int tiles_x, int nz)
     r.i0 = tx * W;
     r.j0 = ty * TY;
     r.jend = min(r.j0 + TY, nz);
+    return r;
+}
+
+// The same with the task height given at run time (the batched kernels, whose
+// groups each have their own).
+template <int W>
+__device__ __forceinline__ Task task_of_rows(long long t, int K, int tiles_x, int nz, int ty)
+{
+    Task r;
+    r.cond = (int)(t % K);
+    const long long sp = t / K;
+    const int tyi = (int)(sp / tiles_x);
+    const int tx = (int)(sp - (long long)tyi * tiles_x);
+    r.i0 = tx * W;
+    r.j0 = tyi * ty;
+    r.jend = min(r.j0 + ty, nz);
     return r;
 }
 
@@ -932,7 +964,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b(const PcgDesc<T> *__
         for (unsigned c = next_task(&sc->task_ctr[1], lane); c < ntasks;
              c = next_task(&sc->task_ctr[1], lane)) {
             const unsigned t = ntasks - 1u - c;
-            const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+            // d.ty: a batched group's own task height (its initial pass runs here)
+            const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
             double val[2];
             run_task_b<T, VEC, INIT>(d, tk, s_k, (T)s_alpha, sy[wp], sw[wp], sa[wp], lane, val);
             publish_unit<2>(val, reducer_of(d), ntasks, t, lane);
@@ -1631,6 +1664,349 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc
     if (reduce_units<2>(reducer_of(d), ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
         threadIdx.x == 0) {
         const int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter, d.guard_limit);
+        if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
+    }
+}
+
+// ------------------------------------------------------------------ phase B, bulk-copied rows
+//
+// The arithmetic and order of run_task_b_staged (so the results are bitwise the
+// same), with the ring filled differently: one lane per warp copies each field's
+// whole row segment, columns i0 - 4 .. i0 + W + 3 (W + 8 elements, halo
+// included), with cp.async.bulk global -> shared, completing on the ring slot's
+// mbarrier (transaction count = the bytes of the row).  The other 31 lanes issue
+// no copy instructions and take no address arithmetic for them.  Slot s of a
+// field row holds column (i0 - 4 + s) mod n_theta; at the periodic seam a row is
+// copied in two pieces (the 16-byte wrap piece and the rest).  Needs
+// n_theta % 4 == 0 (16-byte pieces), n_theta >= W + 8 (at most one wrap per row)
+// and 16-byte aligned fields.
+//
+// Every wait on an mbarrier is bounded: after kBarSpin failed polls the warp
+// records GMAF_TIMEOUT in the run's scalars, stops, waits (again bounded) for
+// the copies it still has in flight and leaves its task loop.
+
+constexpr unsigned kBarSpin = 1u << 22;
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(tx)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete; false if it never did.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned k = 0; k < kBarSpin; ++k)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The per-warp ring of D + 1 slots and their barriers, for one warp.
+template <int D>
+struct BulkRing {
+    unsigned long long *bar;   // [D + 1] mbarriers
+    unsigned parity;           // bit k: phase parity the next wait on slot k expects
+    unsigned pend;             // bit k: slot k has a phase armed and not yet waited for
+    bool ok;                   // false once a wait gave up
+};
+
+template <typename T, int VEC, int TY, bool INIT, int D>
+__device__ __forceinline__ void run_task_b_bulk(const PcgDesc<T> &d, const Task &tk, int k, T alpha,
+                                                T *ring, T *yb, T *wb, BulkRing<D> &br, int lane,
+                                                double (&out)[2])
+{
+    constexpr int W = 32 * VEC;
+    constexpr int NB = W + 8, NF = 5, SLOT = NF * NB;
+    constexpr int kSpare = W + 7;
+    constexpr bool BF = sizeof(T) == 4;
+    const int nth = d.nth, nz = d.nz;
+    const long long n = d.n;
+    const bool assor = (d.precond == 1);
+    RowAcc<T> arz, arr;
+    const size_t off = (size_t)tk.cond * (size_t)n;
+    const size_t coff = (size_t)d.cslot[tk.cond] * (size_t)n;
+    const int c0 = tk.i0 + lane * VEC;
+    const bool owned = c0 < nth;
+    const int g0 = wrap_col(c0, nth);
+    const int sown = 4 + lane * VEC;
+    const int hl = lane < 4 ? lane : 3;
+    const int hoff = hl < 2 ? hl - 2 : W + (hl - 2);
+    const int hg = wrap_col(tk.i0 + hoff, nth);
+    const int hs = hl < 2 ? hl + 2 : W + 2 + hl;
+    const int hslot_y = lane < 4 ? hs : kSpare;
+    const int hslot_w = (lane == 1 || lane == 2) ? hs : kSpare;
+    T *rn = d.r[(k + 1) & 1] + off + (long long)tk.j0 * nth + g0;
+    T *zo = d.z + off + (long long)tk.j0 * nth + g0;
+
+    // copy pieces of a row segment (lane 0): columns [a, b) = [i0 - 4, i0 + W + 4)
+    // mapped into [0, n_theta); a < 0 only when i0 = 0, b > n_theta only at the last tile
+    const int a = tk.i0 - 4, b = tk.i0 + W + 4;
+    const int m_lo = a < 0 ? 0 : a, m_hi = b < nth ? b : nth;
+    const unsigned m_bytes = (unsigned)(m_hi - m_lo) * sizeof(T);
+    const int m_dst = m_lo - a;
+    const int x_src = a < 0 ? a + nth : 0;                 // the wrap piece
+    const int x_dst = a < 0 ? 0 : nth - a;
+    const unsigned x_bytes = a < 0 ? (unsigned)(-a) * sizeof(T) : (b > nth ? (unsigned)(b - nth) * sizeof(T) : 0u);
+    const T *src[NF] = {d.r[k & 1] + off, d.v + off, d.invD + coff, d.aE + coff, d.aN + coff};
+    constexpr int NFR = INIT ? NF - 1 : NF;                // fields copied (no v in the initial pass)
+    const unsigned row_bytes = (unsigned)NFR * (unsigned)NB * sizeof(T);
+
+    auto issue = [&](int jr) {
+        if (jr > tk.jend || !br.ok) return;                 // rows past the task are never consumed
+        br.pend |= 1u << ((jr + 1) % (D + 1));              // (uniform: every lane keeps the mask)
+        if (lane == 0) {
+            unsigned long long *bar = &br.bar[(jr + 1) % (D + 1)];
+            if (jr >= 0 && jr < nz) {
+                T *slot = ring + ((jr + 1) % (D + 1)) * SLOT;
+                const long long rq = (long long)jr * nth;
+                // the slot's last generic reads (an earlier row) precede the async writes
+                fence_proxy_async_smem();
+                mbar_arrive_tx(bar, row_bytes);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (INIT && f == 1) continue;
+                    T *dst = slot + f * NB;
+                    bulk_g2s(dst + m_dst, src[f] + rq + m_lo, m_bytes, bar);
+                    if (x_bytes) bulk_g2s(dst + x_dst, src[f] + rq + x_src, x_bytes, bar);
+                }
+            } else {
+                mbar_arrive(bar);                           // boundary row: nothing to copy
+            }
+        }
+    };
+
+    T y_m1[VEC], w_m1[VEC], od_m1[VEC], n_m1[VEC], e_m1[VEC], r_m1[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = od_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
+    T hy_m1 = T(0), hn_m1 = T(0), he_m1 = T(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
+    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+        issue(jr + D);
+        const int sl = (jr + 1) % (D + 1);
+        if (br.ok) {
+            br.ok = mbar_wait(&br.bar[sl], (br.parity >> sl) & 1u);
+            br.ok = __all_sync(0xffffffffu, br.ok);
+        }
+        if (!br.ok) break;
+        br.parity ^= 1u << sl;
+        br.pend &= ~(1u << sl);
+        const T *cur = ring + sl * SLOT;
+        const bool inrow = jr >= 0 && jr < nz;
+        T r1[VEC], y[VEC], dI[VEC], ev[VEC], nv[VEC];
+        T hy = T(0), hd = T(0), he = T(0), hn = T(0);
+        if (inrow) {
+            T rv[VEC], vx[VEC];
+            Vec<T, VEC>::ldrw(cur + 0 * NB + sown, rv);
+            if (!INIT) Vec<T, VEC>::ldrw(cur + 1 * NB + sown, vx);
+            Vec<T, VEC>::ldrw(cur + 2 * NB + sown, dI);
+            Vec<T, VEC>::ldrw(cur + 3 * NB + sown, ev);
+            Vec<T, VEC>::ldrw(cur + 4 * NB + sown, nv);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                r1[q] = INIT ? rv[q] : rv[q] - alpha * vx[q];
+                y[q] = r1[q] * dI[q];
+            }
+            if (BF || lane < 4) {
+                const T hr = INIT ? cur[hs] : cur[hs] - alpha * cur[NB + hs];
+                hd = cur[2 * NB + hs];
+                he = cur[3 * NB + hs];
+                hn = cur[4 * NB + hs];
+                hy = hr * hd;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) r1[q] = y[q] = dI[q] = ev[q] = nv[q] = T(0);
+        }
+        Vec<T, VEC>::st(yb + sown, y);
+        if (BF || lane < 4) yb[hslot_y] = hy;
+        T aw_wrap = T(0);
+        if (BF) aw_wrap = __shfl_sync(0xffffffffu, he_m1, 1);
+        __syncwarp();
+        T w[VEC], od[VEC];
+        T hw = T(0);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) w[q] = od[q] = T(0);
+        if (assor && inrow && jr >= tk.j0) {
+            const T *ab = cur + 3 * NB;
+            const bool south = jr > 0;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const int s = sown + q, gi = g0 + q;
+                T sum = south ? n_m1[q] * y_m1[q] : T(0);
+                const T aW = (q > 0) ? ev[q - 1] : ab[s - 1];
+                const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
+                if (gi > 0) sum += aW * yW;
+                if (gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
+                od[q] = dI[q];
+                w[q] = y[q] + od[q] * sum;
+            }
+            if (BF || lane == 1 || lane == 2) {
+                T sum = south ? hn_m1 * hy_m1 : T(0);
+                if (hg > 0) sum += ab[hs - 1] * yb[hs - 1];
+                if (hg == nth - 1) sum += he * yb[hs + 1];
+                hw = hy + hd * sum;
+            }
+        }
+        const int jo = jr - 1;
+        if (jo >= tk.j0 && jo < tk.jend) {
+            T zz[VEC];
+            T rz = T(0), rr = T(0);
+            const bool north = jo < nz - 1;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                if (assor) {
+                    const int s = sown + q, gi = g0 + q;
+                    T sum = north ? n_m1[q] * w[q] : T(0);
+                    const T wE = (q < VEC - 1) ? w_m1[q + 1] : wb[s + 1];
+                    if (gi < nth - 1) sum += e_m1[q] * wE;
+                    if (gi == 0)
+                        sum += (BF ? aw_wrap : d.aE[coff + (size_t)jo * nth + nth - 1]) *
+                               ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
+                    zz[q] = w_m1[q] + od_m1[q] * sum;   // Eq. 3.6 without its factor c1
+                } else {
+                    zz[q] = y_m1[q];
+                }
+                rz += r_m1[q] * zz[q];
+                rr += r_m1[q] * r_m1[q];
+            }
+            if (owned) {
+                Vec<T, VEC>::st(zo, zz);
+                if (!INIT) Vec<T, VEC>::st(rn, r_m1);
+                arz.add_row(rz);
+                arr.add_row(rr);
+            }
+            zo += nth;
+            rn += nth;
+        }
+        __syncwarp();
+        if (assor) {
+            Vec<T, VEC>::st(wb + sown, w);
+            if (BF || lane == 1 || lane == 2) wb[hslot_w] = hw;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            y_m1[q] = y[q];
+            w_m1[q] = w[q];
+            od_m1[q] = od[q];
+            n_m1[q] = nv[q];
+            e_m1[q] = ev[q];
+            r_m1[q] = r1[q];
+        }
+        hy_m1 = hy;
+        hn_m1 = hn;
+        he_m1 = he;
+    }
+    out[0] = arz.value();
+    out[1] = arr.value();
+}
+
+// After a wait gave up: wait (bounded) for every phase the warp still has
+// outstanding, so that no copy lands in shared memory after the block exits.
+template <int D>
+__device__ __forceinline__ void bulk_drain(BulkRing<D> &br)
+{
+#pragma unroll
+    for (int sl = 0; sl < D + 1; ++sl)
+        if ((br.pend >> sl) & 1u) mbar_wait(&br.bar[sl], (br.parity >> sl) & 1u);
+    br.pend = 0u;
+}
+
+template <typename T, int VEC, int TY, int MINB, bool INIT, int D>
+__global__ void __launch_bounds__(kThreads, MINB) k_phase_b_bulk(const PcgDesc<T> *__restrict__ dp)
+{
+    using R = RingB<T, VEC>;
+    const PcgDesc<T> &d = *dp;
+    Scalars *sc = d.sc;
+    extern __shared__ __align__(128) unsigned char g_dyn_smem_bk[];
+    __shared__ __align__(8) unsigned long long s_bar[kWarps][D + 1];
+    __shared__ int s_done, s_k;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_k = sc->iter;
+        s_alpha = sc->alpha;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T *mine = reinterpret_cast<T *>(g_dyn_smem_bk) + (size_t)wp * R::per_warp(D);
+    T *ring = mine;
+    T *yb = mine + (D + 1) * R::NF * R::NB;
+    T *wb = yb + R::NB;
+    BulkRing<D> br{s_bar[wp], 0u, 0u, true};
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < D + 1; ++q) mbar_init(&br.bar[q], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const unsigned ntasks = (unsigned)d.ntiles;
+    constexpr int W = 32 * VEC;
+    for (unsigned c = next_task(&sc->task_ctr[1], lane); c < ntasks;
+         c = next_task(&sc->task_ctr[1], lane)) {
+        const unsigned t = ntasks - 1u - c;    // reverse of phase A's order (L2 reuse)
+        double val[2] = {0.0, 0.0};
+        if (br.ok) {
+            const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+            run_task_b_bulk<T, VEC, TY, INIT, D>(d, tk, s_k, (T)s_alpha, ring, yb, wb, br, lane, val);
+            if (!br.ok) {
+                // a wait gave up: record it and drain (bounded) what is in flight; the
+                // warp keeps publishing (zero) sums for the tasks it still takes, so the
+                // launch's reductions complete, and the run ends with GMAF_TIMEOUT
+                if (lane == 0) {
+                    sc->status = GMAF_TIMEOUT;
+                    __threadfence();
+                }
+                bulk_drain<D>(br);
+            }
+        }
+        publish_unit<2>(val, reducer_of(d), ntasks, t, lane);
+    }
+    double tot[2];
+    if (reduce_units<2>(reducer_of(d), ntasks, &sc->ticket[kTicketB], &sc->task_ctr[1], tot) &&
+        threadIdx.x == 0) {
+        int done = finish_b<INIT>(sc, tot[0], tot[1], s_k, d.eps, d.max_iter, d.guard_limit);
+        if (sc->status == GMAF_TIMEOUT) {
+            sc->done = 1;
+            done = 1;
+        }
         if (d.use_cond) cudaGraphSetConditional(d.cond, done ? 0u : 1u);
     }
 }

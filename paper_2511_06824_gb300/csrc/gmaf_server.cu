@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -26,11 +27,48 @@
 
 namespace gmaf {
 
-// Fixed kernel variant for served requests (n_theta % 4 == 0): the task
-// decomposition of a request must not depend on what else is running.
+// Kernel variant of the served requests (n_theta % 4 == 0): 128-column tasks.
+// The batched kernels are one instantiation shared by every group (one
+// persistent kernel per CG phase), so columns per lane and staging are fixed;
+// the task height is per group (PcgDesc::ty), chosen per grid by the tuner
+// below.  A request's task decomposition depends only on its grid, never on
+// what else is running.
 constexpr int kSvVec = 4, kSvTY = 32, kSvMinB = 2;
 constexpr int kSvW = 32 * kSvVec;
 constexpr int kSvStage = 2;            // rows staged ahead by cp.async (0: register prefetch)
+constexpr int kSvTyCand[] = {32, 16, 64};   // tuner candidates, the default first
+constexpr int kSvTyMin = 16;                // smallest candidate (sizes the partial sums)
+
+// Tuner decisions, shared by every server of the process: the first request of
+// a grid on a device fixes the task height of that grid (for the kernel form
+// the server uses), so the same grid is always decomposed the same way.
+struct SvTuneEntry {
+    int dev, nth, nz, staged, ty;
+};
+static std::mutex g_sv_tune_mutex;
+static std::vector<SvTuneEntry> g_sv_tune;
+
+static int sv_tuned_rows(int dev, int nth, int nz, int staged)
+{
+    std::lock_guard<std::mutex> lock(g_sv_tune_mutex);
+    for (const auto &e : g_sv_tune)
+        if (e.dev == dev && e.nth == nth && e.nz == nz && e.staged == staged) return e.ty;
+    return 0;
+}
+
+static int sv_record_rows(int dev, int nth, int nz, int staged, int ty)
+{
+    std::lock_guard<std::mutex> lock(g_sv_tune_mutex);
+    for (const auto &e : g_sv_tune)     // another server may have decided first: keep its pick
+        if (e.dev == dev && e.nth == nth && e.nz == nz && e.staged == staged) return e.ty;
+    g_sv_tune.push_back({dev, nth, nz, staged, ty});
+    return ty;
+}
+
+static long long sv_tasks(int nth, int nz, int ty)
+{
+    return (long long)((nth + kSvW - 1) / kSvW) * ((nz + ty - 1) / ty) * 9;
+}
 
 // The two batched phase kernels of the server and their dynamic shared memory.
 struct SvKernels {
@@ -116,6 +154,7 @@ struct Request {
     gmaf_request in;
     Geom g;
     long long n, N, ntasks;
+    int ty;                       // rows per task (kSvTY until tuned)
     size_t off, bytes;
     // fields carved from the arena block
     double *D, *aE, *aN, *S, *p, *r64, *trig, *conds, *loads, *result, *part;
@@ -133,6 +172,7 @@ struct Request {
     int last_iter, longest;       // inner iteration counter after the last solve; longest solve
     bool cont_run, stalled;       // the last solve continued the recurrence; it stalled
     bool no_progress;             // the last solve made no iteration
+    double rel0, rnorm0;          // FP64 residual at admission (p = 0)
 };
 
 constexpr size_t kHdrBytes = 8192;   // scalars, descriptors, conditions, flags, loads, result
@@ -160,7 +200,7 @@ static int stream_grid_s(long long N, int num_sms)
 static size_t footprint(int nth, int nz, int num_sms)
 {
     const long long n = (long long)nth * nz, N = 9 * n, m = 5 * n;
-    const long long ntasks = (long long)((nth + kSvW - 1) / kSvW) * ((nz + kSvTY - 1) / kSvTY) * 9;
+    const long long ntasks = sv_tasks(nth, nz, kSvTyMin);   // the most tasks any tiling has
     size_t b = kHdrBytes;
     b += Arena::round_up((size_t)4 * nth * sizeof(double));                          // trig
     b += Arena::round_up(partial_doubles_for(ntasks, stream_grid_s(N, num_sms), num_sms) *
@@ -201,6 +241,20 @@ struct gmaf_server {
     MultiDesc<float> hm;
     int grid_m;
     SvKernels kern;
+    int device;
+    int staged;                    // kernel form: rows staged by cp.async (1) or not (0)
+    int tune;                      // tune the task height per grid (GMAF_SV_TUNE, default 1)
+    int use_graph;                 // rounds as CUDA graphs (GMAF_SV_GRAPH, default 1)
+    // tuner: a one-group batched table and two events
+    PcgDesc<float> *d_tune_group;
+    MultiDesc<float> *d_tune_mdesc;
+    cudaEvent_t ev[2];
+    // the round graph: `iters` phase pairs on the batched table, launch grid `grid`
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    std::vector<cudaGraphNode_t> graph_nodes;
+    int graph_grid, graph_iters;
+    const void *graph_a, *graph_b;
 };
 
 namespace gmaf {
@@ -228,7 +282,8 @@ static void carve(gmaf_server *sv, Request *r)
         return q;
     };
     r->trig = (double *)take((size_t)4 * r->g.nth * sizeof(double));
-    r->part = (double *)take(partial_doubles_for(r->ntasks, r->grid_s, sv->num_sms) * sizeof(double));
+    r->part = (double *)take(partial_doubles_for(sv_tasks(r->g.nth, r->g.nz, kSvTyMin), r->grid_s,
+                                                 sv->num_sms) * sizeof(double));
     r->D = (double *)take((size_t)m * 8);
     r->aE = (double *)take((size_t)m * 8);
     r->aN = (double *)take((size_t)m * 8);
@@ -323,8 +378,9 @@ static int admit(gmaf_server *sv, Request *r)
     h.K = 9;
     h.n = r->n;
     h.tiles_x = (r->g.nth + kSvW - 1) / kSvW;
-    h.tiles_y = (r->g.nz + kSvTY - 1) / kSvTY;
+    h.tiles_y = (r->g.nz + r->ty - 1) / r->ty;
     h.ntiles = r->ntasks;
+    h.ty = r->ty;
     h.precond = 1;
     h.zero_init = 1;
     h.use_cond = 0;
@@ -372,6 +428,8 @@ static int admit(gmaf_server *sv, Request *r)
     r->rnorm_prev = 0.0;
     r->last_iter = r->longest = 0;
     r->cont_run = r->stalled = r->no_progress = false;
+    r->rel0 = ho.true_rel;
+    r->rnorm0 = ho.rnorm;
     if (ho.normS == 0.0 || !std::isfinite(ho.true_rel) || ho.true_rel <= r->in.eps) return 1;
     return start_inner(sv, r, ho.true_rel, ho.rnorm);
 }
@@ -402,6 +460,7 @@ static int retire(gmaf_server *sv, Request *r, int status, double true_rel)
     out.iterations = r->total_inner;
     out.outer_iterations = r->outer;
     out.true_rel_residual = true_rel;
+    out.tile_rows = r->ty;
     std::memcpy(out.loads, res, 12 * sizeof(double));
     std::memcpy(out.J, res + 12, 48 * sizeof(double));
     std::memcpy(out.G, res + 60, 4 * sizeof(double));
@@ -445,6 +504,42 @@ static int grow_zeroed(gmaf_server *sv, void **buf, size_t *cap, size_t need)
     return GMAF_OK;
 }
 
+// Grow the partial-sum buffer of the batched launches (no zeroing needed: every
+// task writes its own entries before they are read).
+static int grow_partials(gmaf_server *sv, size_t need)
+{
+    if (need <= sv->mpart_cap) return GMAF_OK;
+    cudaError_t e = cudaStreamSynchronize(sv->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (sv->mpart) cudaFree(sv->mpart);
+    sv->mpart = nullptr;
+    sv->mpart_cap = 0;
+    if (cudaMalloc(&sv->mpart, need) != cudaSuccess) {
+        cudaGetLastError();
+        sv->mpart = nullptr;
+        return GMAF_OUT_OF_MEMORY;
+    }
+    sv->mpart_cap = need;
+    return GMAF_OK;
+}
+
+static int batched_grid(gmaf_server *sv, long long tasks)
+{
+    int per_sm = 0, per_sm_a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv->kern.b, kThreads, sv->kern.smem_b) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, sv->kern.a, kThreads, sv->kern.smem_a) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        per_sm = per_sm_a = 1;
+    }
+    per_sm = std::max(1, std::min(per_sm, per_sm_a));
+    long long gm = (tasks + kWarps - 1) / kWarps;
+    if (gm > (long long)per_sm * sv->num_sms) gm = (long long)per_sm * sv->num_sms;
+    if (gm < 1) gm = 1;
+    return (int)gm;
+}
+
 static int rebuild_table(gmaf_server *sv)
 {
     MultiDesc<float> &hm = sv->hm;
@@ -460,19 +555,8 @@ static int rebuild_table(gmaf_server *sv)
     hm.total_tasks = acc;
     hm.groups = sv->d_groups;
     hm.msc = sv->msc;
-    const size_t need = (size_t)2 * (acc ? acc : 1) * sizeof(double);
-    if (need > sv->mpart_cap) {
-        cudaError_t e = cudaStreamSynchronize(sv->stream);
-        if (e != cudaSuccess) return cuda_status(e);
-        if (sv->mpart) cudaFree(sv->mpart);
-        sv->mpart = nullptr;
-        e = cudaMalloc(&sv->mpart, need);
-        if (e != cudaSuccess) {
-            sv->mpart_cap = 0;
-            return GMAF_OUT_OF_MEMORY;
-        }
-        sv->mpart_cap = need;
-    }
+    int pst = grow_partials(sv, (size_t)2 * (acc ? acc : 1) * sizeof(double));
+    if (pst != GMAF_OK) return pst;
     hm.partials = sv->mpart;
     // two-level reduction: chunks of kChunk tasks, counted per group
     unsigned cacc = 0;
@@ -497,18 +581,165 @@ static int rebuild_table(gmaf_server *sv)
         e = cudaMemcpyAsync(sv->d_mdesc, &hm, sizeof(MultiDesc<float>), cudaMemcpyHostToDevice, sv->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&sv->msc->done, 0, sizeof(int), sv->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    int per_sm = 0, per_sm_a = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv->kern.b, kThreads, sv->kern.smem_b) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, sv->kern.a, kThreads, sv->kern.smem_a) !=
-            cudaSuccess)
-        per_sm = per_sm_a = 1;
-    per_sm = std::max(1, std::min(per_sm, per_sm_a));
-    long long gm = ((long long)acc + kWarps - 1) / kWarps;
-    if (gm > (long long)per_sm * sv->num_sms) gm = (long long)per_sm * sv->num_sms;
-    if (gm < 1) gm = 1;
-    sv->grid_m = (int)gm;
+    sv->grid_m = batched_grid(sv, acc);
     sv->dirty = false;
+    return GMAF_OK;
+}
+
+// Tuner: the time of `reps` batched iterations (phase A + phase B) of request r
+// alone, decomposed into tasks of `ty` rows, on its own data (its inner solve
+// has just been started).  The timed copy of its descriptor never converges;
+// the caller restarts the inner solve afterwards.
+static int time_alone(gmaf_server *sv, Request *r, int ty, int reps, float *ms_out)
+{
+    cudaStream_t s = sv->stream;
+    PcgDesc<float> hh = r->h;
+    hh.ty = ty;
+    hh.tiles_y = (r->g.nz + ty - 1) / ty;
+    hh.ntiles = sv_tasks(r->g.nth, r->g.nz, ty);
+    hh.eps = 1e-300;
+    hh.max_iter = 1 << 30;
+    hh.guard_limit = 0;
+    const unsigned nt = (unsigned)hh.ntiles;
+    const unsigned nch = (nt + kChunk - 1) / kChunk;
+    int st = grow_partials(sv, (size_t)2 * nt * sizeof(double));
+    if (st == GMAF_OK)
+        st = grow_zeroed(sv, (void **)&sv->mchunk, &sv->mchunk_cap, (size_t)2 * nch * sizeof(double));
+    if (st == GMAF_OK)
+        st = grow_zeroed(sv, (void **)&sv->mctr, &sv->mctr_cap, (size_t)(kMaxGroups + nch) * sizeof(unsigned));
+    if (st != GMAF_OK) return st;
+    sv->dirty = true;                 // the batched table must pick up regrown buffers
+    MultiDesc<float> tm{};
+    tm.ngroups = 1;
+    tm.total_tasks = nt;
+    tm.task_off[0] = 0;
+    tm.task_off[1] = nt;
+    tm.groups = sv->d_tune_group;
+    tm.msc = sv->msc;
+    tm.partials = sv->mpart;
+    tm.chunk_off[0] = 0;
+    tm.chunk_off[1] = nch;
+    tm.chunk_sum = sv->mchunk;
+    tm.group_ctr = sv->mctr;
+    tm.chunk_ctr = sv->mctr + kMaxGroups;
+    cudaError_t e = cudaMemcpyAsync(sv->d_tune_group, &hh, sizeof hh, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_tune_mdesc, &tm, sizeof tm, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sv->msc->done, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int grid = batched_grid(sv, nt);
+    void *args[] = {(void *)&sv->d_tune_mdesc};
+    const int warm = 2;
+    for (int q = 0; q < warm + reps && e == cudaSuccess; ++q) {
+        if (q == warm) e = cudaEventRecord(sv->ev[0], s);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(sv->kern.a, dim3(grid), dim3(kThreads), args, sv->kern.smem_a, s);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(sv->kern.b, dim3(grid), dim3(kThreads), args, sv->kern.smem_b, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sv->ev[1], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(sv->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms_out, sv->ev[0], sv->ev[1]);
+    return cuda_status(e);
+}
+
+// Task height of r's grid: the process-wide decision for the grid, or (the first
+// request of the grid) the fastest candidate timed on r alone, in two
+// round-robin passes taking the best time of each; a later candidate replaces
+// the default only when it is more than 3% faster.  r's inner solve is
+// restarted when the tuner ran.
+static int tune_request(gmaf_server *sv, Request *r)
+{
+    int ty = sv_tuned_rows(sv->device, r->g.nth, r->g.nz, sv->staged);
+    if (ty == 0) {
+        float best[3] = {3e38f, 3e38f, 3e38f};
+        int tiles[3];
+        const int nc = (int)(sizeof kSvTyCand / sizeof kSvTyCand[0]);
+        for (int round = 0; round < 2; ++round) {
+            for (int c = 0; c < nc; ++c) {
+                tiles[c] = (r->g.nz + kSvTyCand[c] - 1) / kSvTyCand[c];
+                bool dup = false;                      // same decomposition as an earlier one
+                for (int q = 0; q < c; ++q) dup = dup || tiles[q] == tiles[c];
+                if (dup) continue;
+                float ms = 0.0f;
+                const int st = time_alone(sv, r, kSvTyCand[c], 5, &ms);
+                if (st != GMAF_OK) return st;
+                best[c] = std::min(best[c], ms);
+            }
+        }
+        int pick = 0;
+        for (int c = 1; c < nc; ++c)
+            if (best[c] < 0.97f * best[pick]) pick = c;
+        ty = sv_record_rows(sv->device, r->g.nth, r->g.nz, sv->staged, kSvTyCand[pick]);
+        // restart the inner solve that the timing runs advanced
+        r->ty = ty;
+        r->ntasks = sv_tasks(r->g.nth, r->g.nz, ty);
+        r->h.ty = ty;
+        r->h.tiles_y = (r->g.nz + ty - 1) / ty;
+        r->h.ntiles = r->ntasks;
+        r->outer = 0;
+        r->rnorm_prev = 0.0;
+        return start_inner(sv, r, r->rel0, r->rnorm0);
+    }
+    return GMAF_OK;
+}
+
+// The round graph: `iterations` phase pairs on the batched table.  Rebuilt when
+// the round length or the kernels change; when only the launch grid changed
+// (the active set grew or shrank) its kernel nodes are updated in place.
+static void destroy_round_graph(gmaf_server *sv)
+{
+    if (sv->graph_exec) cudaGraphExecDestroy(sv->graph_exec);
+    if (sv->graph) cudaGraphDestroy(sv->graph);
+    sv->graph_exec = nullptr;
+    sv->graph = nullptr;
+    sv->graph_nodes.clear();
+    sv->graph_iters = 0;
+}
+
+static int round_graph(gmaf_server *sv, int iterations)
+{
+    void *args[] = {(void *)&sv->d_mdesc};
+    cudaKernelNodeParams kp{};
+    kp.blockDim = dim3(kThreads);
+    kp.gridDim = dim3(sv->grid_m);
+    kp.kernelParams = args;
+    if (sv->graph_exec && sv->graph_iters == iterations && sv->graph_a == sv->kern.a &&
+        sv->graph_b == sv->kern.b) {
+        if (sv->graph_grid == sv->grid_m) return GMAF_OK;
+        cudaError_t e = cudaSuccess;
+        for (size_t q = 0; q < sv->graph_nodes.size() && e == cudaSuccess; ++q) {
+            const bool a = (q & 1) == 0;
+            kp.func = (void *)(a ? sv->kern.a : sv->kern.b);
+            kp.sharedMemBytes = (unsigned)(a ? sv->kern.smem_a : sv->kern.smem_b);
+            e = cudaGraphExecKernelNodeSetParams(sv->graph_exec, sv->graph_nodes[q], &kp);
+        }
+        if (e == cudaSuccess) {
+            sv->graph_grid = sv->grid_m;
+            return GMAF_OK;
+        }
+        cudaGetLastError();               // fall through: rebuild
+    }
+    destroy_round_graph(sv);
+    cudaError_t e = cudaGraphCreate(&sv->graph, 0);
+    cudaGraphNode_t prev = nullptr;
+    for (int q = 0; q < 2 * iterations && e == cudaSuccess; ++q) {
+        const bool a = (q & 1) == 0;
+        kp.func = (void *)(a ? sv->kern.a : sv->kern.b);
+        kp.sharedMemBytes = (unsigned)(a ? sv->kern.smem_a : sv->kern.smem_b);
+        cudaGraphNode_t node = nullptr;
+        e = cudaGraphAddKernelNode(&node, sv->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e == cudaSuccess) sv->graph_nodes.push_back(node);
+        prev = node;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sv->graph_exec, sv->graph, 0);
+    if (e != cudaSuccess) {
+        destroy_round_graph(sv);
+        return cuda_status(e);
+    }
+    sv->graph_iters = iterations;
+    sv->graph_grid = sv->grid_m;
+    sv->graph_a = sv->kern.a;
+    sv->graph_b = sv->kern.b;
     return GMAF_OK;
 }
 
@@ -625,12 +856,29 @@ int gmaf_server_create(gmaf_ctx *ctx, size_t hbm_budget_bytes, gmaf_server **out
     sv->dirty = true;
     sv->hm = MultiDesc<float>{};
     sv->grid_m = 1;
+    sv->device = ctx->device;
     const char *stg = std::getenv("GMAF_SV_STAGED");
-    sv->kern = sv_kernels(!(stg && std::atoi(stg) == 0));
+    sv->staged = (stg && std::atoi(stg) == 0) ? 0 : 1;
+    sv->kern = sv_kernels(sv->staged != 0);
+    const char *tn = std::getenv("GMAF_SV_TUNE");
+    sv->tune = (tn && std::atoi(tn) == 0) ? 0 : 1;
+    const char *gr = std::getenv("GMAF_SV_GRAPH");
+    sv->use_graph = (gr && std::atoi(gr) == 0) ? 0 : 1;
+    sv->d_tune_group = nullptr;
+    sv->d_tune_mdesc = nullptr;
+    sv->ev[0] = sv->ev[1] = nullptr;
+    sv->graph = nullptr;
+    sv->graph_exec = nullptr;
+    sv->graph_grid = sv->graph_iters = 0;
+    sv->graph_a = sv->graph_b = nullptr;
     cudaError_t e = cudaMalloc(&sv->base, sv->budget);
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_mdesc, sizeof(MultiDesc<float>));
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_groups, kMaxGroups * sizeof(PcgDesc<float>));
     if (e == cudaSuccess) e = cudaMalloc(&sv->msc, sizeof(Scalars));
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_tune_group, sizeof(PcgDesc<float>));
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_tune_mdesc, sizeof(MultiDesc<float>));
+    if (e == cudaSuccess) e = cudaEventCreate(&sv->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&sv->ev[1]);
     if (e == cudaSuccess) e = cudaMemsetAsync(sv->msc, 0, sizeof(Scalars), sv->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -638,6 +886,10 @@ int gmaf_server_create(gmaf_ctx *ctx, size_t hbm_budget_bytes, gmaf_server **out
         if (sv->d_mdesc) cudaFree(sv->d_mdesc);
         if (sv->d_groups) cudaFree(sv->d_groups);
         if (sv->msc) cudaFree(sv->msc);
+        if (sv->d_tune_group) cudaFree(sv->d_tune_group);
+        if (sv->d_tune_mdesc) cudaFree(sv->d_tune_mdesc);
+        for (cudaEvent_t ev : sv->ev)
+            if (ev) cudaEventDestroy(ev);
         delete sv;
         return GMAF_OUT_OF_MEMORY;
     }
@@ -656,6 +908,10 @@ int gmaf_server_destroy(gmaf_server *sv)
     cudaFree(sv->d_mdesc);
     cudaFree(sv->d_groups);
     cudaFree(sv->msc);
+    cudaFree(sv->d_tune_group);
+    cudaFree(sv->d_tune_mdesc);
+    for (cudaEvent_t ev : sv->ev) cudaEventDestroy(ev);
+    destroy_round_graph(sv);
     if (sv->mpart) cudaFree(sv->mpart);
     if (sv->mchunk) cudaFree(sv->mchunk);
     if (sv->mctr) cudaFree(sv->mctr);
@@ -680,8 +936,8 @@ int gmaf_server_submit(gmaf_server *sv, const gmaf_request *req, int64_t *id_out
     r->g = make_geom(&req->grid, &req->phys, &req->tex);
     r->n = (long long)req->grid.n_theta * req->grid.n_z;
     r->N = 9 * r->n;
-    r->ntasks = (long long)((req->grid.n_theta + kSvW - 1) / kSvW) *
-                ((req->grid.n_z + kSvTY - 1) / kSvTY) * 9;
+    r->ty = kSvTY;                     // the tuned height is looked up at admission
+    r->ntasks = sv_tasks(req->grid.n_theta, req->grid.n_z, r->ty);
     r->grid_s = stream_grid_s(r->N, sv->num_sms);
     r->bytes = bytes;
     sv->queue.push_back(r);
@@ -700,7 +956,12 @@ int gmaf_server_run(gmaf_server *sv, int32_t iterations, int32_t *active_out, in
         if (!sv->arena.alloc(r->bytes, &off)) break;
         sv->queue.pop_front();
         r->off = off;
+        // the grid's tuned task height, when decided; else the default until tuned
+        const int known = sv_tuned_rows(sv->device, r->g.nth, r->g.nz, sv->staged);
+        r->ty = known ? known : kSvTY;
+        r->ntasks = sv_tasks(r->g.nth, r->g.nz, r->ty);
         st = admit(sv, r);
+        if (st == GMAF_OK && sv->tune && !known) st = tune_request(sv, r);
         if (st == 1) {                        // nothing to solve: retire at once
             st = retire(sv, r, GMAF_OK, 0.0);
             if (st != GMAF_OK) return st;
@@ -718,14 +979,19 @@ int gmaf_server_run(gmaf_server *sv, int32_t iterations, int32_t *active_out, in
         if (sv->dirty && (st = rebuild_table(sv))) return st;
         cudaError_t e0 = cudaMemsetAsync(&sv->msc->done, 0, sizeof(int), sv->stream);
         if (e0 != cudaSuccess) return cuda_status(e0);
-        void *args[] = {(void *)&sv->d_mdesc};
         cudaError_t e = cudaSuccess;
-        for (int it = 0; it < iterations && e == cudaSuccess; ++it) {
-            e = cudaLaunchKernel(sv->kern.a, dim3(sv->grid_m), dim3(kThreads), args, sv->kern.smem_a,
-                                 sv->stream);
-            if (e == cudaSuccess)
-                e = cudaLaunchKernel(sv->kern.b, dim3(sv->grid_m), dim3(kThreads), args, sv->kern.smem_b,
+        if (sv->use_graph) {
+            if ((st = round_graph(sv, iterations))) return st;
+            e = cudaGraphLaunch(sv->graph_exec, sv->stream);
+        } else {
+            void *args[] = {(void *)&sv->d_mdesc};
+            for (int it = 0; it < iterations && e == cudaSuccess; ++it) {
+                e = cudaLaunchKernel(sv->kern.a, dim3(sv->grid_m), dim3(kThreads), args, sv->kern.smem_a,
                                      sv->stream);
+                if (e == cudaSuccess)
+                    e = cudaLaunchKernel(sv->kern.b, dim3(sv->grid_m), dim3(kThreads), args,
+                                         sv->kern.smem_b, sv->stream);
+            }
         }
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
@@ -783,6 +1049,7 @@ int gmaf_server_cancel(gmaf_server *sv, int64_t id)
     gmaf_result out{};
     out.id = r->id;
     out.status = GMAF_CANCELLED;
+    out.tile_rows = r->ty;
     out.iterations = r->total_inner;
     out.outer_iterations = r->outer;
     out.state = r->in.state;

@@ -9,15 +9,23 @@ The eccentricity at the start of a step is the converged one of the previous
 step (backward difference, Eq. 2.22).
 
 The paper gives no formula for the external and inertia loads (Eq. 2.10 names
-them only); the march uses a synthetic side load from the swash plate, the
-chamber force times tan(10 deg) (swash angle of Table 8) scaled by `kappa`,
-acting at the case end of the gap (generalized force on e3).  The default
-kappa = 0.2 keeps the eccentricity below 0.6 c over a revolution of the oracle
-on a 48 x 24 grid with the seeded trapezoid pressure (bound asked: 0.8 c).  The
-load always acts along +x and nothing in the model restores the centred
-position, so on finer textured grids the eccentricity keeps growing under load:
-on the textured 1024 x 512 gap it reaches the wall within the first revolution
-(shaft step 76 with kappa = 0.2, in FP64 as in mixed precision).
+them only).  The march uses:
+- a synthetic side load from the swash plate, the chamber force times
+  tan(10 deg) (swash angle of Table 8) scaled by `kappa`, acting at the case
+  end of the gap (generalized force on e3).  The load always acts along +x and
+  nothing in the model restores the centred position, so under a steady load
+  the eccentricity keeps growing; kappa is calibrated so that the march stays
+  within 0.8 c (see the benchmark's dynamics mode for the configured value);
+- the piston's inertia F_I = -M e'' (Eq. 2.10) with the piston mass m_K of
+  Table 8 spread evenly over the coupling length: the virtual work of -rho x''
+  over the linear tilt x(z) = (1 - z/L) e1 + (z/L) e3 (likewise y with e2, e4)
+  gives the generalized mass matrix M = m_K [[1/3, 1/6], [1/6, 1/3]] per
+  direction.  e'' is the backward difference (edot - edot_l) / dt of the rate,
+  as Eq. 2.22 uses for e.  It enters each Picard iteration through F_ext,
+  evaluated at the iterate's rate (lagged by one iteration: the device update
+  does not include the -M / dt term in its Jacobian, which for this piston is
+  about 1e-4 of the squeeze-film damping), so a converged step balances
+  oil, side load and inertia exactly.
 
 Everything per Picard iteration runs on the device through the C ABI; this
 module is the host loop.  The pressure fields stay in the library's context and
@@ -35,6 +43,7 @@ import numpy as np
 from . import gmaf
 
 SWASH_ANGLE_DEG = 10.0
+PISTON_MASS = 0.128          # m_K of Table 8 [kg]
 
 
 def side_load(p_chamber: float, radius: float, kappa: float) -> np.ndarray:
@@ -44,6 +53,31 @@ def side_load(p_chamber: float, radius: float, kappa: float) -> np.ndarray:
     at z = L; its virtual work on the linear tilt loads e3 only."""
     f = kappa * p_chamber * math.pi * radius ** 2 * math.tan(math.radians(SWASH_ANGLE_DEG))
     return np.array([0.0, 0.0, f, 0.0])
+
+
+def inertia_matrix(mass: float) -> np.ndarray:
+    """Generalized mass matrix of a piston of `mass` spread evenly over the coupling
+    length, on the coordinates (e1, e2, e3, e4): the kinetic energy of the linear
+    tilt x(z) = (1 - t) e1 + t e3, y(z) = (1 - t) e2 + t e4 (t = z / L) is
+    1/2 edot^T M edot with M = mass [[1/3, 1/6], [1/6, 1/3]] in each direction."""
+    a, b = mass / 3.0, mass / 6.0
+    return np.array([[a, 0.0, b, 0.0], [0.0, a, 0.0, b], [b, 0.0, a, 0.0], [0.0, b, 0.0, a]])
+
+
+def inertia_force(M: np.ndarray, edot, edot_prev, dt: float) -> np.ndarray:
+    """F_I = -M e'' with e'' = (edot - edot_prev) / dt (backward difference)."""
+    return -M @ ((np.asarray(edot, dtype=np.float64) - np.asarray(edot_prev, dtype=np.float64)) / dt)
+
+
+def gpu_stepper(ctx: int) -> Callable:
+    """The Picard step of the library (general or simplified scheme) on context ctx."""
+    def step(scheme, n_theta, n_z, ph, tex, state, e_prev, dt, F_ext, d_e, d_edot, opts):
+        if scheme == "simplified":
+            return gmaf.gmaf_picard_step_simplified(ctx, n_theta, n_z, ph, tex, state, dt, F_ext,
+                                                    d_edot, opts)
+        return gmaf.gmaf_picard_step(ctx, n_theta, n_z, ph, tex, state, e_prev, dt, F_ext, d_e,
+                                     d_edot, opts)
+    return step
 
 
 @dataclass
@@ -83,16 +117,22 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
           kappa: float = 0.2, tol_F: float = 1e-6, max_picard: int = 20,
           d_e: float = 2e-8, d_edot: float = 1e-6, opts: Optional[gmaf.gmaf_solver_opts] = None,
           on_step: Optional[Callable[[StepRecord], None]] = None,
-          scheme: str = "general") -> Trajectory:
+          scheme: str = "general", mass: float = PISTON_MASS,
+          stepper: Optional[Callable] = None) -> Trajectory:
     """Run `steps` shaft-angle steps.  p_profile[s % steps_per_rev] is the chamber
     pressure of step s; the sliding speed is v_amp * sin(phi).
 
     scheme "general": the double-Jacobian Picard iteration (Eq. 2.12-2.19, 9 conditions).
     scheme "simplified": the conventional one (Eq. 2.20-2.22, 5 conditions); each time
     step starts from the predictor e = e_l + dt edot_l, so that the increments of
-    Eq. 2.22 keep e = e_l + dt edot, the backward difference, at every iterate."""
+    Eq. 2.22 keep e = e_l + dt edot, the backward difference, at every iterate.
+    mass: piston mass of the inertia load (0 leaves it out).
+    stepper: the Picard step to call (default: the library's, on ctx); same arguments
+    as the callable gpu_stepper returns."""
     if scheme not in ("general", "simplified"):
         raise ValueError(f"unknown scheme {scheme!r}")
+    step_fn = stepper or gpu_stepper(ctx)
+    M = inertia_matrix(mass)
     phys = np.asarray(phys, dtype=np.float64).copy()
     dt = (60.0 / rpm) / steps_per_rev
     state = np.asarray(state0, dtype=np.float64).copy()
@@ -106,9 +146,10 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
         ph = phys.copy()
         ph[5] = float(p_profile[s % steps_per_rev])
         ph[4] = v_amp * math.sin(phi)
-        F_ext = side_load(ph[5], ph[0], kappa)
-        scale = max(float(np.linalg.norm(F_ext)), 1.0)
+        F_side = side_load(ph[5], ph[0], kappa)
+        scale = max(float(np.linalg.norm(F_side)), 1.0)
         e_prev = state[:4].copy()
+        edot_prev = state[4:].copy()
         if scheme == "simplified":
             state[:4] = e_prev + dt * state[4:]
         converged = False
@@ -118,12 +159,8 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
         it = 0
         for it in range(1, max_picard + 1):
             oo = o if first_solve else warm
-            if scheme == "simplified":
-                r = gmaf.gmaf_picard_step_simplified(ctx, n_theta, n_z, ph, tex, state, dt, F_ext,
-                                                     d_edot, oo)
-            else:
-                r = gmaf.gmaf_picard_step(ctx, n_theta, n_z, ph, tex, state, e_prev, dt, F_ext, d_e,
-                                          d_edot, oo)
+            F_ext = F_side + inertia_force(M, state[4:], edot_prev, dt)
+            r = step_fn(scheme, n_theta, n_z, ph, tex, state, e_prev, dt, F_ext, d_e, d_edot, oo)
             first_solve = False
             pcg += r["iters"]
             G_norm = float(np.linalg.norm(r["G"]))

@@ -82,7 +82,7 @@ class gmaf_result(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("outer_iterations", ctypes.c_int32), ("true_rel_residual", ctypes.c_double),
                 ("state", gmaf_state), ("loads", ctypes.c_double * 12), ("J", ctypes.c_double * 48),
-                ("G", ctypes.c_double * 4)]
+                ("G", ctypes.c_double * 4), ("tile_rows", ctypes.c_int32)]
 
 
 class GmafError(RuntimeError):
@@ -411,7 +411,8 @@ def gmaf_request_footprint(n_theta: int, n_z: int) -> int:
 def result_dict(r: gmaf_result) -> dict:
     return dict(id=r.id, status=r.status, iters=r.iterations, outer=r.outer_iterations,
                 true_rel=r.true_rel_residual, state=state_vector(r.state),
-                loads=np.array(r.loads), J=np.array(r.J).reshape(6, 8), G=np.array(r.G))
+                loads=np.array(r.loads), J=np.array(r.J).reshape(6, 8), G=np.array(r.G),
+                tile_rows=r.tile_rows)
 
 
 class Server:

@@ -66,7 +66,7 @@ int main(void) {
   printf("gmaf_request %zu\n", sizeof(gmaf_request));
   printf("gmaf_result %zu\n", sizeof(gmaf_result));
   P(gmaf_request, state) P(gmaf_request, dt) P(gmaf_request, max_iter)
-  P(gmaf_result, state) P(gmaf_result, J) P(gmaf_result, G)
+  P(gmaf_result, state) P(gmaf_result, J) P(gmaf_result, G) P(gmaf_result, tile_rows)
   P(gmaf_texture, radius) P(gmaf_texture, offset_z) P(gmaf_state, edot)
   P(gmaf_solver_opts, omega) P(gmaf_solver_opts, eps) P(gmaf_solver_opts, max_iter)
   P(gmaf_solver_opts, precision) P(gmaf_solver_opts, zero_init) P(gmaf_solver_opts, criterion)

@@ -22,8 +22,13 @@ def g():
     return gmaf
 
 
-def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, max_picard=20):
+def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, max_picard=20,
+                 mass=0.128):
+    """The march with the oracle's Picard step: side load on e3, and the inertia of a
+    piston of `mass` spread evenly over the gap, -M (edot - edot_l) / dt with
+    M = mass / 6 [[2, 1], [1, 2]] on (e1, e3) and on (e2, e4)."""
     dt = (60.0 / 600.0) / 360.0
+    M = mass / 6.0 * np.array([[2, 0, 1, 0], [0, 2, 0, 1], [1, 0, 2, 0], [0, 1, 0, 2.0]])
     out = []
     for s in range(steps):
         phi = 2 * math.pi * (s % 360) / 360
@@ -33,8 +38,10 @@ def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, ma
         f = kappa * ph[5] * math.pi * ph[0] ** 2 * math.tan(math.radians(10.0))
         F = np.array([0.0, 0.0, f, 0.0])
         e_prev = st[:4].copy()
+        ed_prev = st[4:].copy()
         for _ in range(max_picard):
-            r = oracle.picard_step(nth, nz, ph, tex, st, e_prev, dt, F, 2e-8, 1e-6, eps=eps)
+            Fi = F - M @ ((st[4:] - ed_prev) / dt)
+            r = oracle.picard_step(nth, nz, ph, tex, st, e_prev, dt, Fi, 2e-8, 1e-6, eps=eps)
             assert r["status"] == 0
             if np.linalg.norm(r["G"]) <= tol_F * max(np.linalg.norm(F), 1.0):
                 break
@@ -43,8 +50,11 @@ def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, ma
     return np.array(out)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-6), (1, 1e-4)])
-def test_march_matches_oracle(g, precision, tol):
+@pytest.mark.parametrize("precision,tol,mass", [(0, 1e-6, 0.128), (1, 1e-4, 0.128),
+                                                (0, 1e-6, 30.0), (0, 1e-6, 0.0)])
+def test_march_matches_oracle(g, precision, tol, mass):
+    """Mass 0.128 kg is the piston of Table 8; 30 kg makes the inertia load visible
+    on this grid; 0 leaves it out."""
     from paper_2511_06824_gb300 import dynamics
     nth, nz, steps = 48, 24, 10
     phys = inputs.phys_vector()
@@ -54,8 +64,8 @@ def test_march_matches_oracle(g, precision, tol):
     eps = 1e-12
     with g.Context() as c:
         traj = dynamics.march(c.handle, nth, nz, phys, tex, st0, prof, steps, kappa=0.2,
-                              opts=g.solver_opts(eps=eps, precision=precision))
-    ref = oracle_march(nth, nz, phys, tex, st0.copy(), prof, steps, 0.2, eps)
+                              opts=g.solver_opts(eps=eps, precision=precision), mass=mass)
+    ref = oracle_march(nth, nz, phys, tex, st0.copy(), prof, steps, 0.2, eps, mass=mass)
     got = traj.states
     assert all(r.converged for r in traj.records)
     scale = np.abs(ref[:, :4]).max()

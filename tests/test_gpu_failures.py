@@ -42,9 +42,9 @@ def system(nth=96, nz=40, K=3, seed=1):
     return (nth, nz, K), dev(D), dev(aE), dev(aN), dev(S)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision,criterion", [(0, 0), (1, 0), (0, 1)])
 @pytest.mark.parametrize("where", ["nan_in_S", "inf_in_D"])
-def test_nonfinite_input_is_reported_and_the_context_stays_usable(g, precision, where):
+def test_nonfinite_input_is_reported_and_the_context_stays_usable(g, precision, criterion, where):
     (nth, nz, K), D, aE, aN, S = system()
     bad_D, bad_S = D.clone(), S.clone()
     i = K * nth * nz // 2 + 17
@@ -52,7 +52,7 @@ def test_nonfinite_input_is_reported_and_the_context_stays_usable(g, precision, 
         bad_S[i] = float("nan")
     else:
         bad_D[i] = float("inf")
-    opts = g.solver_opts(eps=1e-10, precision=precision)
+    opts = g.solver_opts(eps=1e-10, precision=precision, criterion=criterion)
     with g.Context() as c:
         p = torch.zeros_like(S)
         st, _, _ = g.gmaf_solve_joint(c.handle, nth, nz, K, bad_D, aE, aN, bad_S, p, opts,
@@ -64,8 +64,11 @@ def test_nonfinite_input_is_reported_and_the_context_stays_usable(g, precision, 
     with g.Context() as c2:
         p2 = torch.zeros_like(S)
         g.gmaf_solve_joint(c2.handle, nth, nz, K, D, aE, aN, S, p2, opts)
-    assert torch.equal(p1, p2)
+    # (not bitwise: the first context tuned its kernels on the non-finite system and
+    # may use another variant for this shape; the FP64 / mixed parity bounds hold)
     assert torch.isfinite(p1).all()
+    tol = 1e-6 if precision else 1e-9
+    assert float(torch.linalg.norm(p1 - p2) / torch.linalg.norm(p2)) <= tol
 
 
 def test_nonfinite_state_is_refused_before_any_work(g):

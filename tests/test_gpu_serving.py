@@ -123,3 +123,36 @@ def test_stream_replay_runs_and_reports_latency(g, ctx):
     out = serving.serve_stream(ctx, its, 8 << 30, eps=1e-10, round_iters=32)
     assert out["completed"] == 6 and out["p99_ms"] >= out["p50_ms"] > 0
     assert all(r["status"] == 0 for r in out["results"])
+
+
+def test_graph_rounds_match_host_driven_rounds(g, ctx, monkeypatch):
+    """A round as a CUDA graph (default) and as host launches run the same kernels on
+    the same table in the same order: bitwise the same results and counts."""
+    its = items([(128, 64, True), (256, 48, True), (64, 32, False)], seed=13)
+    monkeypatch.setenv("GMAF_SV_GRAPH", "0")
+    host, _ = run_all(g, ctx, its, round_iters=24)
+    monkeypatch.setenv("GMAF_SV_GRAPH", "1")
+    graph, _ = run_all(g, ctx, its, round_iters=24)
+    for a, b in zip(host, graph):
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["iters"] == b["iters"] and a["outer"] == b["outer"]
+        for key in ("loads", "J", "G", "state"):
+            assert np.array_equal(a[key], b[key]), key
+
+
+def test_tile_height_is_tuned_once_per_grid(g, ctx):
+    """The tuner fixes each grid's task height at the first request of that grid; a
+    later server, another mix or another order decomposes the grid the same way and
+    gives bitwise the same results."""
+    its = items([(128, 64, True), (128, 64, False), (512, 128, True), (64, 32, True)], seed=17)
+    first, _ = run_all(g, ctx, its)
+    again, _ = run_all(g, ctx, its[::-1])
+    again = again[::-1]
+    rows = {}
+    for a, b, it in zip(first, again, its):
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["tile_rows"] in (16, 32, 64)
+        assert rows.setdefault((it.n_theta, it.n_z), a["tile_rows"]) == a["tile_rows"]
+        assert b["tile_rows"] == a["tile_rows"]
+        for key in ("loads", "J", "G", "state"):
+            assert np.array_equal(a[key], b[key]), key
