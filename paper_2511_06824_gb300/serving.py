@@ -96,6 +96,15 @@ def serve_stream(ctx: int, items: List[StreamItem], hbm_budget_bytes: int, eps: 
     return out
 
 
+def reference_step(ctx: int, it: StreamItem, eps: float = 1e-12, omega: float = 1.2,
+                   d_e: float = 2e-8, d_edot: float = 1e-6) -> dict:
+    """The request's Picard step as one FP64 joint solve (gmaf_picard_step) at a tight
+    eps: the accuracy reference of the equal-accuracy comparison."""
+    return gmaf.gmaf_picard_step(ctx, it.n_theta, it.n_z, it.phys, it.tex, it.state, it.state[:4],
+                                 DT, it.F_ext, d_e, d_edot,
+                                 gmaf.solver_opts(precond=1, omega=omega, eps=eps, precision=0))
+
+
 def sequential_step(ctx: int, it: StreamItem, eps: float, omega: float = 1.2, d_e: float = 2e-8,
                     d_edot: float = 1e-6) -> dict:
     """One Picard step the sequential way: 9 single-condition FP64 solves."""

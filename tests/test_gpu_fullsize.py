@@ -9,11 +9,17 @@ oracle's matrix, the loads and the 6 x 8 Jacobian from the oracle's integration,
 the generalized force and the state update from numpy's 4 x 4 solve -- and the
 assembly against the oracle's entry by entry.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2511_06824_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "textured-2048x1024-k9_seed0_oracle_eps1e-10.json")
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -140,3 +146,45 @@ def test_benchmark_workload_refinement_modes(g, monkeypatch):
     assert out["far"][1]["iterations"] <= 4 * it_r
     for name in ("restarted", "far"):
         assert load_err(out[name][0]["loads"], out["continued"][0]["loads"]) <= 1e-6, name
+
+
+@pytest.mark.parametrize("precision,p_tol,load_tol", [(0, 1e-9, 1e-7), (1, 1e-6, 1e-5)])
+def test_benchmark_workload_step_matches_the_stored_oracle_step(g, precision, p_tol, load_tol):
+    """The benchmark's Picard step (textured 2048 x 1024 x 9, seed 0, eps 1e-10) in
+    both precisions against the oracle's own step of the same system, stored by
+    tests/golden/make_textured_2048x1024_k9_oracle.py: pressure at 1000 seeded cells
+    of every condition and the full-field norms, the loads, the Jacobian, the
+    generalized force and the update."""
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    w = inputs.make(gold["workload"], gold["seed"])
+    nth, nz, n = w.n_theta, w.n_z, w.n
+    assert np.array_equal(w.state, gold["state_in"])
+    opts = g.solver_opts(eps=gold["eps"], omega=gold["omega"], precision=precision)
+    with g.Context() as c:
+        r = g.gmaf_picard_step(c.handle, nth, nz, w.phys, w.tex, w.state, w.state[:4], gold["dt"],
+                               np.array(gold["F_ext"]), gold["d_e"], gold["d_edot"], opts)
+        p = torch.zeros(9 * n, dtype=torch.float64, device="cuda")
+        g.gmaf_last_fields(c.handle, nth, nz, p)
+        torch.cuda.synchronize()
+    assert r["status"] == 0
+    p = p.view(9, n)
+    idx = torch.tensor(gold["sample_index"], device="cuda")
+    pg = p[:, idx].cpu().numpy()
+    po = np.array(gold["p_samples"])
+    assert np.linalg.norm(pg - po) <= p_tol * np.linalg.norm(po)
+    for k in range(9):
+        assert np.linalg.norm(pg[k] - po[k]) <= p_tol * np.linalg.norm(po[k]), k
+    norms = torch.linalg.norm(p, dim=1).cpu().numpy()
+    np.testing.assert_allclose(norms, gold["p_norm"], rtol=p_tol)
+    lo = np.array(gold["loads_all"])
+    assert load_err(r["loads"], lo[0]) <= load_tol
+    Jo = np.array(gold["J"])
+    colscale = np.abs(Jo).max(axis=0, keepdims=True)
+    # the Jacobian is a forward difference over steps of 1e-3 c: load errors grow by ~1e3
+    assert np.max(np.abs(r["J"] - Jo) / colscale) <= 1e3 * load_tol
+    Go = np.array(gold["G"])
+    assert np.max(np.abs(r["G"] - Go)) <= load_tol * np.abs(Go).max()
+    so = np.array(gold["state_out"])
+    ds_g, ds_o = r["state"] - w.state, so - w.state
+    assert np.linalg.norm(ds_g - ds_o) <= 1e3 * load_tol * np.linalg.norm(ds_o)

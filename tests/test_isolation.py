@@ -46,7 +46,7 @@ def test_oracle_shares_no_code_with_the_package():
 
 def test_bench_reaches_the_oracle_only_from_its_cpu_legs():
     tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
-    allowed = {"oracle_sample", "run_reference"}
+    allowed = {"oracle_sample", "run_reference", "cpu_baseline"}
     hits = []
 
     class V(ast.NodeVisitor):
