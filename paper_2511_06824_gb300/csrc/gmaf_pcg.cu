@@ -88,7 +88,62 @@ static KernelSet<T> ks_bulk_ab()
     return ks;
 }
 
-constexpr int kMaxVariants = 16;
+// Both phases staged as ks_staged_ab, with phase B's row loop unrolled over its
+// ring of DB + 1 slots (compile-time slots); id + 4000000.
+template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
+static KernelSet<T> ks_staged_ab_unrolled()
+{
+    KernelSet<T> ks = ks_staged_ab<T, VEC, TY, MINB, DA, DB>();
+    const void *b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, DB, true>;
+    const void *bi = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, DB, true>;
+    static std::atomic<unsigned long long> done_b{0}, done_bi{0};
+    smem_optin(done_b, b, ks.smem_b);
+    smem_optin(done_bi, bi, ks.smem_b);
+    ks.b = b;
+    ks.b_init = bi;
+    ks.id += 4000000;
+    return ks;
+}
+
+// Both phases staged, with both row loops unrolled over their rings; id + 8000000.
+template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
+static KernelSet<T> ks_staged_ab_unrolled2()
+{
+    KernelSet<T> ks = ks_staged_ab_unrolled<T, VEC, TY, MINB, DA, DB>();
+    const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA, true>;
+    static std::atomic<unsigned long long> done_a{0};
+    smem_optin(done_a, a, ks.smem_a);
+    ks.a = a;
+    ks.id += 4000000;
+    return ks;
+}
+
+// Both phases staged as ks_staged_ab, in blocks of NT threads (MINB blocks per SM);
+// id + 100000000 * (NT / 32).
+template <typename T, int VEC, int TY, int MINB, int DA, int NT>
+static KernelSet<T> ks_staged_ab_nt(int rows = TY)
+{
+    KernelSet<T> ks{};
+    constexpr int warps = NT / 32;
+    ks.smem_b = (size_t)warps * RingB<T, VEC>::per_warp(DA) * sizeof(T);
+    ks.smem_a = (size_t)warps * RingA<T, VEC, sizeof(T) == 4>::per_warp(DA) * sizeof(T);
+    ks.a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA, false, NT>;
+    ks.b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, DA, false, NT>;
+    ks.b_init = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, DA, false, NT>;
+    static std::atomic<unsigned long long> done_a{0}, done_b{0}, done_bi{0};
+    smem_optin(done_a, ks.a, ks.smem_a);
+    smem_optin(done_b, ks.b, ks.smem_b);
+    smem_optin(done_bi, ks.b_init, ks.smem_b);
+    ks.W = 32 * VEC;
+    ks.TY = rows;           // rows per task, taken by the staged kernels from the descriptor
+    ks.id = 100000000 * warps + 200000 * DA + 100000 * DA + 1000 * VEC + 10 * rows + MINB;
+    ks.sched = 0;
+    ks.p_period = sizeof(T) == 4 ? 2 : 1;
+    ks.threads = NT;
+    return ks;
+}
+
+constexpr int kMaxVariants = 24;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
 static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bool bulk_ok = false)
@@ -99,6 +154,12 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bo
         // schedule keep every warp busy on smaller ones (1024 x 512 x 9 has only
         // 1152 tasks of 32 rows for 2432 resident warps)
         out[n++] = ks_staged_ab<float, 4, 32, 2, 2>();
+        out[n++] = ks_staged_ab_unrolled<float, 4, 32, 2, 2>();
+        out[n++] = ks_staged_ab_unrolled2<float, 4, 32, 2, 2>();
+        // 3 blocks of 6 warps per SM (18 warps, 94 registers); the task height is a
+        // run-time choice: with equal tasks the phase lasts whole waves of tasks, and
+        // on 2048 x 1024 x 9 18-row tasks fill exactly 3 waves of the 2736 warps
+        for (int rows : {32, 24, 20, 18, 16}) out[n++] = ks_staged_ab_nt<float, 4, 32, 3, 2, 192>(rows);
         if (bulk_ok) out[n++] = ks_bulk_ab<float, 4, 32, 2, 2>();
         out[n++] = ks_staged_ab<float, 4, 16, 2, 2>();
         out[n++] = ks_of<float, 4, 32, 2>(0);
@@ -182,6 +243,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
     kp.blockDim = dim3(kThreads);
     kp.kernelParams = args;
     if (e == cudaSuccess) {
+        kp.blockDim = dim3(run.ks.threads);
         kp.func = (void *)run.ks.b_init;
         kp.gridDim = dim3(run.grid_b);
         kp.sharedMemBytes = (unsigned)run.ks.smem_b;
@@ -214,6 +276,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
         }
     }
     if (e == cudaSuccess) {
+        kp.blockDim = dim3(kThreads);
         kp.func = (void *)k_finalize<T>;
         kp.gridDim = dim3(run.grid_s);
         kp.sharedMemBytes = 0;
@@ -242,6 +305,7 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
 {
     PcgDesc<T> &h = run.h;
     run.ks = ks;
+    h.ty = ks.TY;        // the staged kernels' task height (the others use their template's)
     h.tiles_x = (h.nth + ks.W - 1) / ks.W;
     h.tiles_y = (h.nz + ks.TY - 1) / ks.TY;
     h.ntiles = (long long)h.tiles_x * h.tiles_y * h.K;
@@ -264,8 +328,8 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
         h.sgroups = G;
         run.grid_a = run.grid_b = (int)((warps + kWarps - 1) / kWarps);
     } else {
-        run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms, ks.smem_a);
-        run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b);
+        run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms, ks.smem_a, ks.threads);
+        run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b, ks.threads);
     }
     run.grid_s = stream_grid(h.n * h.K, ctx->num_sms);
 }
@@ -331,12 +395,12 @@ static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand
             GMAF_CUDA(cudaMemcpyAsync(tr.d_desc, &tr.h, sizeof(PcgDesc<T>), cudaMemcpyHostToDevice, s));
             k_reset<<<1, 32, 0, s>>>(tr.h.sc, 0);
             k_init_r<T><<<tr.grid_s, kThreads, 0, s>>>(tr.d_desc);
-            GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s, tr.ks.smem_b));
+            GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s, tr.ks.smem_b, tr.ks.threads));
             const int warm = 3, reps = 10;
             for (int q = 0; q < warm + reps; ++q) {
                 if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
-                GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s, tr.ks.smem_a));
-                GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s, tr.ks.smem_b));
+                GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s, tr.ks.smem_a, tr.ks.threads));
+                GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s, tr.ks.smem_b, tr.ks.threads));
             }
             GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
             GMAF_CUDA(cudaEventSynchronize(ctx->ev[1]));
@@ -486,7 +550,7 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
     int *it_h = (int *)ctx->pinned;        // iter, first, done of the scalars
     PhaseClock clk{ctx};
     clk.begin(s);
-    GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s, run.ks.smem_b));
+    GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s, run.ks.smem_b, run.ks.threads));
     clk.end(s, 2);
     const int chunk = 16;
     int prev_iter = -1;
@@ -499,10 +563,10 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
         if (it_h[2]) break;
         for (int q = 0; q < chunk; ++q) {
             clk.begin(s);
-            GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s, run.ks.smem_a));
+            GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s, run.ks.smem_a, run.ks.threads));
             clk.end(s, 0);
             clk.begin(s);
-            GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s, run.ks.smem_b));
+            GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s, run.ks.smem_b, run.ks.threads));
             clk.end(s, 1);
         }
     }

@@ -10,10 +10,11 @@
 
 namespace gmaf {
 
-static int grid_for(const void *kernel, long long work_items, int num_sms, size_t smem = 0)
+static int grid_for(const void *kernel, long long work_items, int num_sms, size_t smem = 0,
+                    int threads = kThreads)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     long long g = (long long)per_sm * num_sms;
@@ -50,6 +51,7 @@ struct KernelSet {
     int sched;
     size_t smem_a;             // dynamic shared memory of the phase-A kernel
     int p_period;              // iterations between two p updates of phase A (1 or 2)
+    int threads = kThreads;    // threads per block of both phase kernels
 };
 
 // id = 1000 VEC + 10 TY + MINB (dynamic), 1000000 + 1000 VEC + MINB (static).
@@ -77,17 +79,19 @@ static bool vec_ok(const PcgDesc<T> &h)
 
 template <typename T>
 static cudaError_t launch(const void *fn, int grid, const PcgDesc<T> *dd, cudaStream_t s,
-                         size_t smem = 0)
+                         size_t smem = 0, int threads = kThreads)
 {
     void *args[] = {(void *)&dd};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
 }
 
 // Blocks for a persistent phase kernel: enough to hold every task's warp, at
 // most what stays resident.
-static int phase_grid(const void *kernel, long long ntasks, int num_sms, size_t smem = 0)
+static int phase_grid(const void *kernel, long long ntasks, int num_sms, size_t smem = 0,
+                      int threads = kThreads)
 {
-    return grid_for(kernel, (ntasks + kWarps - 1) / kWarps, num_sms, smem);
+    const int warps = threads / 32;
+    return grid_for(kernel, (ntasks + warps - 1) / warps, num_sms, smem, threads);
 }
 
 // ---------------------------------------------------------------- ASSOR-I

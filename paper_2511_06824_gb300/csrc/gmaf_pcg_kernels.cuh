@@ -723,6 +723,9 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
         const int c0 = tk.i0 + lane * VEC;
         const bool owned = c0 < nth;
         const int g0 = wrap_col(c0, nth);
+        // n_theta % VEC == 0: only element 0 of a lane can be column 0 and only
+        // element VEC - 1 column n_theta - 1 (the seam tests below are static otherwise)
+        const bool at_w = g0 == 0, at_e = g0 + VEC == nth;
         const int sown = 4 + lane * VEC;
         // halo: lanes 0..3 -> columns i0-2, i0-1 (slots 2, 3), i0+W, i0+W+1 (slots W+4, W+5)
         const int hl = lane < 4 ? lane : 3;
@@ -798,12 +801,13 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
             if (assor && inrow && jr >= tk.j0) {
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    const int s = sown + q, gi = g0 + q;
+                    const int s = sown + q;
                     T sum = T(0);
                     if (jr > 0) sum += n_m1[q] * y_m1[q];                            // south
-                    if (gi > 0)                                                        // west
+                    if (q > 0 || !at_w)                                                // west
                         sum += ((q > 0) ? cur.e[q - 1] : ab[s - 1]) * ((q > 0) ? y[q - 1] : yb[s - 1]);
-                    if (gi == nth - 1) sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);  // east, wrapped
+                    if (q == VEC - 1 && at_e)                                          // east, wrapped
+                        sum += cur.e[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
                     od[q] = cur.dI[q];
                     w[q] = y[q] + od[q] * sum;
                 }
@@ -828,11 +832,11 @@ __device__ __forceinline__ void run_task_b(const PcgDesc<T> &d, const Task &tk, 
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
                     if (assor) {
-                        const int s = sown + q, gi = g0 + q;
+                        const int s = sown + q;
                         T sum = T(0);
                         if (jo < nz - 1) sum += n_m1[q] * w[q];                                          // north
-                        if (gi < nth - 1) sum += e_m1[q] * ((q < VEC - 1) ? w_m1[q + 1] : wb[s + 1]);    // east
-                        if (gi == 0)                                                                     // west, wrapped
+                        if (q < VEC - 1 || !at_e) sum += e_m1[q] * ((q < VEC - 1) ? w_m1[q + 1] : wb[s + 1]);  // east
+                        if (q == 0 && at_w)                                                              // west, wrapped
                             sum += (BF ? aw_wrap : __ldg(aE + (size_t)jo * nth + nth - 1)) *
                                    ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
                         zz[q] = w_m1[q] + od_m1[q] * sum;      // Eq. 3.6 without its factor c1
@@ -1240,7 +1244,7 @@ struct RingA {
     __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
 };
 
-template <typename T, int VEC, int TY, int D, bool PAIR = false>
+template <typename T, int VEC, int TY, int D, bool PAIR = false, bool UNR = false>
 __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const Task &tk, int k,
                                                     int first, int pend, T alpha_prev, T alpha_pp,
                                                     T beta, T *ring, T *ub, T *ab, int lane)
@@ -1275,9 +1279,10 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
     // fields: 0 z, 1 u', 2 D, 3 aE, 4 aN, 5 p (, 6 u'': the direction before u')
     const T *src[7] = {d.z + off, uo_base + off, d.D + coff, d.aE + coff, d.aN + coff, pp, un};
 
-    auto issue = [&](int jr) {
+    // ring slot of row jr: (jr - (j0 - 1)) mod (D + 1), passed in by the caller
+    auto issue = [&](int jr, int sl) {
         if (jr >= 0 && jr < nz && jr >= tk.j0 - 1 && jr <= tk.jend) {
-            T *slot = ring + ((jr + 1) % (D + 1)) * SLOT;
+            T *slot = ring + sl * SLOT;
             const size_t rq = (size_t)jr * nth;
             const bool in = jr >= tk.j0 && jr < tk.jend;
 #pragma unroll
@@ -1304,12 +1309,13 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
     for (int q = 0; q < VEC; ++q)
         u_m1[q] = u_m2[q] = uo_m1[q] = D_m1[q] = e_m1[q] = n_m1[q] = n_m2[q] = p_m1[q] = upp_m1[q] = T(0);
 #pragma unroll
-    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
-    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
-        issue(jr + D);
+    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q, q);
+    // one row step: row jr in ring slot sl
+    auto step = [&](const int jr, const int sl) {
+        issue(jr + D, sl == 0 ? D : sl - 1);
         cp_wait<D>();
         __syncwarp();
-        const T *cur = ring + ((jr + 1) % (D + 1)) * SLOT;
+        const T *cur = ring + sl * SLOT;
         const bool inrow = jr >= 0 && jr < nz;
         const bool in = inrow && jr >= tk.j0 && jr < tk.jend;
         T zv[VEC], uov[VEC], Dv[VEC], ev[VEC], nv[VEC], pv[VEC], uppv[VEC];
@@ -1380,6 +1386,21 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             p_m1[q] = pv[q];
             upp_m1[q] = uppv[q];
         }
+    };
+    if constexpr (UNR) {
+        // D + 1 steps per trip with the slots known at compile time, then the rest
+        int jr = tk.j0 - 1;
+        for (; jr + D <= tk.jend; jr += D + 1) {
+#pragma unroll
+            for (int u = 0; u <= D; ++u) step(jr + u, u);
+        }
+        for (int sl = 0; jr <= tk.jend; ++jr, ++sl) step(jr, sl);
+    } else {
+        int sl = 0;
+        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+            step(jr, sl);
+            sl = sl == D ? 0 : sl + 1;
+        }
     }
     cp_wait<0>();
     __syncwarp();
@@ -1387,8 +1408,8 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
 }
 
 // FP32: the p updates are paired (PAIR above); FP64 adds one every iteration.
-template <typename T, int VEC, int TY, int MINB, int D>
-__global__ void __launch_bounds__(kThreads, MINB) k_phase_a_staged(const PcgDesc<T> *__restrict__ dp)
+template <typename T, int VEC, int TY, int MINB, int D, bool UNR = false, int NT = kThreads>
+__global__ void __launch_bounds__(NT, MINB) k_phase_a_staged(const PcgDesc<T> *__restrict__ dp)
 {
     constexpr bool PAIR = sizeof(T) == 4;
     using R = RingA<T, VEC, PAIR>;
@@ -1420,10 +1441,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_a_staged(const PcgDesc
     T *ub = mine + (D + 1) * R::NF * R::NB;
     T *ab = ub + R::NB;
     const unsigned ntasks = (unsigned)d.ntiles;
+    // (tasks are claimed one at a time, when the warp is free: claiming the next one
+    // early scatters the tasks that run together and costs their L2 sharing, 8 %)
     for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
          t = next_task(&sc->task_ctr[0], lane)) {
-        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
-        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR>(
+        const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
+        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR, UNR>(
             d, tk, s_k, s_first, s_pend, (T)s_alpha, (T)s_alpha_pp, (T)s_beta, ring, ub, ab, lane)};
         publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
     }
@@ -1446,7 +1469,7 @@ struct RingB {
 // FP64 pipe, where it measured faster): interior tasks take a second body
 // (EDGE = false: the strip and its halo touch neither theta edge, 2 <= i0 and
 // i0 + W + 2 <= n_theta), with the periodic-wrap tests compiled out.
-template <typename T, int VEC, int TY, bool INIT, int D, bool EDGE>
+template <typename T, int VEC, int TY, bool INIT, int D, bool EDGE, bool UNR = false>
 __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Task &tk, int k,
                                                   T alpha, T *ring, T *yb, T *wb, int lane,
                                                   double (&out)[2])
@@ -1466,6 +1489,9 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     const int c0 = tk.i0 + lane * VEC;
     const bool owned = c0 < nth;
     const int g0 = EDGE ? wrap_col(c0, nth) : c0;
+    // n_theta % VEC == 0: only element 0 of a lane can be column 0 and only
+    // element VEC - 1 column n_theta - 1 (the seam tests below are static otherwise)
+    const bool at_w = g0 == 0, at_e = g0 + VEC == nth;
     const int sown = 4 + lane * VEC;
     const int hl = lane < 4 ? lane : 3;
     const int hoff = hl < 2 ? hl - 2 : W + (hl - 2);
@@ -1480,9 +1506,10 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     T *rn = d.r[(k + 1) & 1] + off + (long long)tk.j0 * nth + g0;
     T *zo = d.z + off + (long long)tk.j0 * nth + g0;
 
-    auto issue = [&](int jr) {
+    // ring slot of row jr: (jr - (j0 - 1)) mod (D + 1), passed in by the caller
+    auto issue = [&](int jr, int sl) {
         if (jr >= 0 && jr < nz && jr <= tk.jend) {
-            T *slot = ring + ((jr + 1) % (D + 1)) * SLOT;
+            T *slot = ring + sl * SLOT;
             const long long rq = row0 + (long long)(jr - tk.j0 + 1) * nth;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -1506,12 +1533,13 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     for (int q = 0; q < VEC; ++q) y_m1[q] = w_m1[q] = od_m1[q] = n_m1[q] = e_m1[q] = r_m1[q] = T(0);
     T hy_m1 = T(0), hn_m1 = T(0), he_m1 = T(0);
 #pragma unroll
-    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q);
-    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
-        issue(jr + D);
+    for (int q = 0; q < D; ++q) issue(tk.j0 - 1 + q, q);
+    // one row step: row jr in ring slot sl
+    auto step = [&](const int jr, const int sl) {
+        issue(jr + D, sl == 0 ? D : sl - 1);
         cp_wait<D>();
         __syncwarp();
-        const T *cur = ring + ((jr + 1) % (D + 1)) * SLOT;
+        const T *cur = ring + sl * SLOT;
         const bool inrow = jr >= 0 && jr < nz;
         T r1[VEC], y[VEC], dI[VEC], ev[VEC], nv[VEC];
         T hy = T(0), hd = T(0), he = T(0), hn = T(0);
@@ -1554,12 +1582,12 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
             const bool south = jr > 0;
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-                const int s = sown + q, gi = g0 + q;
+                const int s = sown + q;
                 T sum = south ? n_m1[q] * y_m1[q] : T(0);
                 const T aW = (q > 0) ? ev[q - 1] : ab[s - 1];
                 const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
-                if (!EDGE || gi > 0) sum += aW * yW;
-                if (EDGE && gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
+                if (!EDGE || q > 0 || !at_w) sum += aW * yW;
+                if (EDGE && q == VEC - 1 && at_e) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
                 od[q] = dI[q];
                 w[q] = y[q] + od[q] * sum;
             }
@@ -1578,11 +1606,11 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
                 if (assor) {
-                    const int s = sown + q, gi = g0 + q;
+                    const int s = sown + q;
                     T sum = north ? n_m1[q] * w[q] : T(0);
                     const T wE = (q < VEC - 1) ? w_m1[q + 1] : wb[s + 1];
-                    if (!EDGE || gi < nth - 1) sum += e_m1[q] * wE;
-                    if (EDGE && gi == 0)
+                    if (!EDGE || q < VEC - 1 || !at_e) sum += e_m1[q] * wE;
+                    if (EDGE && q == 0 && at_w)
                         sum += (BF ? aw_wrap : __ldg(aE + (size_t)jo * nth + nth - 1)) *
                                ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
                     zz[q] = w_m1[q] + od_m1[q] * sum;   // Eq. 3.6 without its factor c1
@@ -1619,6 +1647,23 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         hy_m1 = hy;
         hn_m1 = hn;
         he_m1 = he;
+    };
+    if constexpr (UNR) {
+        // D + 1 steps per trip with the slots known at compile time (no slot
+        // arithmetic, and the rows carried in registers rotate without moves), then
+        // the 0..D rows left
+        int jr = tk.j0 - 1;
+        for (; jr + D <= tk.jend; jr += D + 1) {
+#pragma unroll
+            for (int u = 0; u <= D; ++u) step(jr + u, u);
+        }
+        for (int sl = 0; jr <= tk.jend; ++jr, ++sl) step(jr, sl);
+    } else {
+        int sl = 0;
+        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+            step(jr, sl);
+            sl = sl == D ? 0 : sl + 1;
+        }
     }
     cp_wait<0>();
     __syncwarp();
@@ -1626,8 +1671,8 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     out[1] = arr.value();
 }
 
-template <typename T, int VEC, int TY, int MINB, bool INIT, int D>
-__global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc<T> *__restrict__ dp)
+template <typename T, int VEC, int TY, int MINB, bool INIT, int D, bool UNR = false, int NT = kThreads>
+__global__ void __launch_bounds__(NT, MINB) k_phase_b_staged(const PcgDesc<T> *__restrict__ dp)
 {
     using R = RingB<T, VEC>;
     const PcgDesc<T> &d = *dp;
@@ -1653,11 +1698,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_staged(const PcgDesc
          c = next_task(&sc->task_ctr[1], lane)) {
         const unsigned t = ntasks - 1u - c;    // reverse of phase A's order (L2 reuse)
         double val[2];
-        const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+        const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
         if (sizeof(T) == 8 && tk.i0 >= 2 && tk.i0 + W + 2 <= d.nth)
-            run_task_b_staged<T, VEC, TY, INIT, D, false>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
+            run_task_b_staged<T, VEC, TY, INIT, D, false, UNR>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
         else
-            run_task_b_staged<T, VEC, TY, INIT, D, true>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
+            run_task_b_staged<T, VEC, TY, INIT, D, true, UNR>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
         publish_unit<2>(val, reducer_of(d), ntasks, t, lane);
     }
     double tot[2];
@@ -1763,6 +1808,7 @@ __device__ __forceinline__ void run_task_b_bulk(const PcgDesc<T> &d, const Task 
     const int c0 = tk.i0 + lane * VEC;
     const bool owned = c0 < nth;
     const int g0 = wrap_col(c0, nth);
+    const bool at_w = g0 == 0, at_e = g0 + VEC == nth;   // (see run_task_b_staged)
     const int sown = 4 + lane * VEC;
     const int hl = lane < 4 ? lane : 3;
     const int hoff = hl < 2 ? hl - 2 : W + (hl - 2);
@@ -1867,12 +1913,12 @@ __device__ __forceinline__ void run_task_b_bulk(const PcgDesc<T> &d, const Task 
             const bool south = jr > 0;
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-                const int s = sown + q, gi = g0 + q;
+                const int s = sown + q;
                 T sum = south ? n_m1[q] * y_m1[q] : T(0);
                 const T aW = (q > 0) ? ev[q - 1] : ab[s - 1];
                 const T yW = (q > 0) ? y[q - 1] : yb[s - 1];
-                if (gi > 0) sum += aW * yW;
-                if (gi == nth - 1) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
+                if (q > 0 || !at_w) sum += aW * yW;
+                if (q == VEC - 1 && at_e) sum += ev[q] * ((q < VEC - 1) ? y[q + 1] : yb[s + 1]);
                 od[q] = dI[q];
                 w[q] = y[q] + od[q] * sum;
             }
@@ -1891,11 +1937,11 @@ __device__ __forceinline__ void run_task_b_bulk(const PcgDesc<T> &d, const Task 
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
                 if (assor) {
-                    const int s = sown + q, gi = g0 + q;
+                    const int s = sown + q;
                     T sum = north ? n_m1[q] * w[q] : T(0);
                     const T wE = (q < VEC - 1) ? w_m1[q + 1] : wb[s + 1];
-                    if (gi < nth - 1) sum += e_m1[q] * wE;
-                    if (gi == 0)
+                    if (q < VEC - 1 || !at_e) sum += e_m1[q] * wE;
+                    if (q == 0 && at_w)
                         sum += (BF ? aw_wrap : d.aE[coff + (size_t)jo * nth + nth - 1]) *
                                ((q > 0) ? w_m1[q - 1] : wb[s - 1]);
                     zz[q] = w_m1[q] + od_m1[q] * sum;   // Eq. 3.6 without its factor c1
@@ -1984,7 +2030,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_phase_b_bulk(const PcgDesc<T
         const unsigned t = ntasks - 1u - c;    // reverse of phase A's order (L2 reuse)
         double val[2] = {0.0, 0.0};
         if (br.ok) {
-            const Task tk = task_of<W, TY>(t, d.K, d.tiles_x, d.nz);
+            const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
             run_task_b_bulk<T, VEC, TY, INIT, D>(d, tk, s_k, (T)s_alpha, ring, yb, wb, br, lane, val);
             if (!br.ok) {
                 // a wait gave up: record it and drain (bounded) what is in flight; the

@@ -43,7 +43,8 @@ def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, ma
             Fi = F - M @ ((st[4:] - ed_prev) / dt)
             r = oracle.picard_step(nth, nz, ph, tex, st, e_prev, dt, Fi, 2e-8, 1e-6, eps=eps)
             assert r["status"] == 0
-            if np.linalg.norm(r["G"]) <= tol_F * max(np.linalg.norm(F), 1.0):
+            scale = max(np.linalg.norm(F), ph[5] * math.pi * ph[0] ** 2, 1.0)
+            if np.linalg.norm(r["G"]) <= tol_F * scale:
                 break
             st = r["state"]
         out.append(st.copy())

@@ -19,7 +19,7 @@ import oracle
 from paper_2511_06824_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
-                      "textured-2048x1024-k9_seed0_oracle_eps1e-10.json")
+                      "textured-2048x1024-k9_seed0_oracle_eps{:.0e}.json")
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -148,15 +148,19 @@ def test_benchmark_workload_refinement_modes(g, monkeypatch):
         assert load_err(out[name][0]["loads"], out["continued"][0]["loads"]) <= 1e-6, name
 
 
-@pytest.mark.parametrize("precision,p_tol,load_tol", [(0, 1e-9, 1e-7), (1, 1e-6, 1e-5)])
-def test_benchmark_workload_step_matches_the_stored_oracle_step(g, precision, p_tol, load_tol):
-    """The benchmark's Picard step (textured 2048 x 1024 x 9, seed 0, eps 1e-10) in
-    both precisions against the oracle's own step of the same system, stored by
+@pytest.mark.parametrize("precision,eps,p_tol,load_tol", [(0, 1e-10, 1e-9, 1e-7),
+                                                          (1, 1e-10, 1e-6, 1e-5),
+                                                          (0, 1e-12, 1e-9, 1e-7)])
+def test_benchmark_workload_step_matches_the_stored_oracle_step(g, precision, eps, p_tol, load_tol):
+    """The benchmark's Picard step (textured 2048 x 1024 x 9, seed 0) in both
+    precisions against the oracle's own step of the same system at the same eps
+    (the benchmark's 1e-10, and 1e-12 as well for FP64), stored by
     tests/golden/make_textured_2048x1024_k9_oracle.py: pressure at 1000 seeded cells
     of every condition and the full-field norms, the loads, the Jacobian, the
     generalized force and the update."""
-    with open(GOLDEN) as f:
+    with open(GOLDEN.format(eps)) as f:
         gold = json.load(f)
+    assert gold["eps"] == eps
     w = inputs.make(gold["workload"], gold["seed"])
     nth, nz, n = w.n_theta, w.n_z, w.n
     assert np.array_equal(w.state, gold["state_in"])

@@ -281,7 +281,9 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
 
 # dynamic tasks (ids 1000 VEC + 10 TY + MINB), phase B staged D rows ahead
 # (+ 100000 D), both phases staged (+ 300000 D), phase B filled by bulk copies
-# (+ 2000000), and the static schedule with phase A marching against phase B
+# (+ 2000000), phase B's row loop unrolled over its ring (+ 4000000, both phases
+# + 8000000), blocks of 6 warps with a run-time task height (+ 600000000), and the
+# static schedule with phase A marching against phase B
 # (ids 1000000 + 1000 VEC + MINB); float VEC > 1 kernels need n_theta % 4 == 0,
 # double ones an even n_theta, the bulk-copied phase B n_theta >= 136
 @pytest.mark.parametrize("precision,variant,nth,nz,K", [
@@ -289,6 +291,10 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
     (1, 204162, 132, 45, 9), (1, 204322, 260, 70, 3), (1, 604322, 132, 45, 9),
     (1, 604322, 260, 70, 3), (1, 604162, 132, 45, 9),
     (1, 2604322, 136, 45, 9), (1, 2604322, 260, 70, 3), (1, 2604322, 384, 33, 2),
+    (1, 4604322, 132, 45, 9), (1, 4604322, 260, 70, 3), (1, 4604322, 64, 3, 2),
+    (1, 8604322, 132, 45, 9), (1, 8604322, 260, 70, 3), (1, 8604322, 64, 3, 2),
+    (1, 600604183, 132, 45, 9), (1, 600604183, 260, 70, 3), (1, 600604323, 132, 45, 9),
+    (1, 600604163, 64, 3, 2),
     (1, 1001004, 131, 7, 3), (0, 2322, 130, 45, 9), (0, 1002002, 130, 45, 9),
     (0, 1001003, 131, 7, 3), (0, 1001003, 3, 2, 1),
 ])
@@ -311,19 +317,20 @@ def test_each_schedule_matches_oracle(g, monkeypatch, precision, variant, nth, n
         assert rel_l2(p, po) <= 1e-6
 
 
-@pytest.mark.parametrize("nth,nz,K", [(136, 45, 9), (260, 70, 3), (2048, 64, 2)])
-def test_bulk_copied_phase_b_is_bitwise_the_staged_one(g, monkeypatch, nth, nz, K):
+@pytest.mark.parametrize("nth,nz,K", [(136, 45, 9), (260, 70, 3), (2048, 64, 2), (136, 31, 2)])
+def test_phase_b_forms_are_bitwise_the_staged_one(g, monkeypatch, nth, nz, K):
     """The bulk-copied phase B (one lane copies whole row segments, halo and seam
-    pieces included) feeds the same arithmetic in the same order as the cp.async
-    staged one: bitwise the same solution and iteration count, at the narrowest
-    eligible grid (136 columns), a ragged last tile (260 = 2 x 128 + 4) and the
-    benchmark's width."""
+    pieces included) and the one with its row loop unrolled over the ring feed the
+    same arithmetic in the same order as the cp.async staged one: bitwise the same
+    solution and iteration count, at the narrowest grid the bulk copies take (136
+    columns), a ragged last tile (260 = 2 x 128 + 4), the benchmark's width, and
+    tasks whose row count leaves every remainder of the unrolled loop (31 rows)."""
     conds = states(K, seed=nth + 3)
     so, D, aE, aN, S = oracle.assemble_joint(nth, nz, PHYS, tex_dimples(), conds)
     args = [dev(D), dev(aE), dev(aN), dev(S)]
     n = K * nth * nz
     outs = []
-    for variant in ("604322", "2604322"):
+    for variant in ("604322", "2604322", "4604322", "8604322"):
         monkeypatch.setenv("GMAF_VARIANT", variant)
         c = g.Context()
         try:
@@ -335,8 +342,9 @@ def test_bulk_copied_phase_b_is_bitwise_the_staged_one(g, monkeypatch, nth, nz, 
             c.close()
         assert info["kernel_variant"] == int(variant)
         outs.append((host(p), it, info["outer_iterations"]))
-    assert outs[0][1:] == outs[1][1:]
-    assert np.array_equal(outs[0][0], outs[1][0])
+    for o in outs[1:]:
+        assert o[1:] == outs[0][1:]
+        assert np.array_equal(o[0], outs[0][0])
 
 
 @pytest.mark.parametrize("variant", [1002002, 1001003])
