@@ -88,36 +88,6 @@ static KernelSet<T> ks_bulk_ab()
     return ks;
 }
 
-// Both phases staged as ks_staged_ab, with phase B's row loop unrolled over its
-// ring of DB + 1 slots (compile-time slots); id + 4000000.
-template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
-static KernelSet<T> ks_staged_ab_unrolled()
-{
-    KernelSet<T> ks = ks_staged_ab<T, VEC, TY, MINB, DA, DB>();
-    const void *b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, DB, true>;
-    const void *bi = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, DB, true>;
-    static std::atomic<unsigned long long> done_b{0}, done_bi{0};
-    smem_optin(done_b, b, ks.smem_b);
-    smem_optin(done_bi, bi, ks.smem_b);
-    ks.b = b;
-    ks.b_init = bi;
-    ks.id += 4000000;
-    return ks;
-}
-
-// Both phases staged, with both row loops unrolled over their rings; id + 8000000.
-template <typename T, int VEC, int TY, int MINB, int DA, int DB = DA>
-static KernelSet<T> ks_staged_ab_unrolled2()
-{
-    KernelSet<T> ks = ks_staged_ab_unrolled<T, VEC, TY, MINB, DA, DB>();
-    const void *a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA, true>;
-    static std::atomic<unsigned long long> done_a{0};
-    smem_optin(done_a, a, ks.smem_a);
-    ks.a = a;
-    ks.id += 4000000;
-    return ks;
-}
-
 // Both phases staged as ks_staged_ab, in blocks of NT threads (MINB blocks per SM);
 // id + 100000000 * (NT / 32).
 template <typename T, int VEC, int TY, int MINB, int DA, int NT>
@@ -127,9 +97,9 @@ static KernelSet<T> ks_staged_ab_nt(int rows = TY)
     constexpr int warps = NT / 32;
     ks.smem_b = (size_t)warps * RingB<T, VEC>::per_warp(DA) * sizeof(T);
     ks.smem_a = (size_t)warps * RingA<T, VEC, sizeof(T) == 4>::per_warp(DA) * sizeof(T);
-    ks.a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA, false, NT>;
-    ks.b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, DA, false, NT>;
-    ks.b_init = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, DA, false, NT>;
+    ks.a = (const void *)k_phase_a_staged<T, VEC, TY, MINB, DA, NT>;
+    ks.b = (const void *)k_phase_b_staged<T, VEC, TY, MINB, false, DA, NT>;
+    ks.b_init = (const void *)k_phase_b_staged<T, VEC, TY, MINB, true, DA, NT>;
     static std::atomic<unsigned long long> done_a{0}, done_b{0}, done_bi{0};
     smem_optin(done_a, ks.a, ks.smem_a);
     smem_optin(done_b, ks.b, ks.smem_b);
@@ -154,8 +124,6 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bo
         // schedule keep every warp busy on smaller ones (1024 x 512 x 9 has only
         // 1152 tasks of 32 rows for 2432 resident warps)
         out[n++] = ks_staged_ab<float, 4, 32, 2, 2>();
-        out[n++] = ks_staged_ab_unrolled<float, 4, 32, 2, 2>();
-        out[n++] = ks_staged_ab_unrolled2<float, 4, 32, 2, 2>();
         // 3 blocks of 6 warps per SM (18 warps, 94 registers); the task height is a
         // run-time choice: with equal tasks the phase lasts whole waves of tasks, and
         // on 2048 x 1024 x 9 18-row tasks fill exactly 3 waves of the 2736 warps

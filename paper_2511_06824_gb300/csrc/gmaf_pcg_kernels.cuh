@@ -1244,7 +1244,7 @@ struct RingA {
     __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
 };
 
-template <typename T, int VEC, int TY, int D, bool PAIR = false, bool UNR = false>
+template <typename T, int VEC, int TY, int D, bool PAIR = false>
 __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const Task &tk, int k,
                                                     int first, int pend, T alpha_prev, T alpha_pp,
                                                     T beta, T *ring, T *ub, T *ab, int lane)
@@ -1387,20 +1387,10 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             upp_m1[q] = uppv[q];
         }
     };
-    if constexpr (UNR) {
-        // D + 1 steps per trip with the slots known at compile time, then the rest
-        int jr = tk.j0 - 1;
-        for (; jr + D <= tk.jend; jr += D + 1) {
-#pragma unroll
-            for (int u = 0; u <= D; ++u) step(jr + u, u);
-        }
-        for (int sl = 0; jr <= tk.jend; ++jr, ++sl) step(jr, sl);
-    } else {
-        int sl = 0;
-        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
-            step(jr, sl);
-            sl = sl == D ? 0 : sl + 1;
-        }
+    int sl = 0;
+    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+        step(jr, sl);
+        sl = sl == D ? 0 : sl + 1;
     }
     cp_wait<0>();
     __syncwarp();
@@ -1408,7 +1398,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
 }
 
 // FP32: the p updates are paired (PAIR above); FP64 adds one every iteration.
-template <typename T, int VEC, int TY, int MINB, int D, bool UNR = false, int NT = kThreads>
+template <typename T, int VEC, int TY, int MINB, int D, int NT = kThreads>
 __global__ void __launch_bounds__(NT, MINB) k_phase_a_staged(const PcgDesc<T> *__restrict__ dp)
 {
     constexpr bool PAIR = sizeof(T) == 4;
@@ -1446,7 +1436,7 @@ __global__ void __launch_bounds__(NT, MINB) k_phase_a_staged(const PcgDesc<T> *_
     for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
          t = next_task(&sc->task_ctr[0], lane)) {
         const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
-        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR, UNR>(
+        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR>(
             d, tk, s_k, s_first, s_pend, (T)s_alpha, (T)s_alpha_pp, (T)s_beta, ring, ub, ab, lane)};
         publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
     }
@@ -1469,7 +1459,7 @@ struct RingB {
 // FP64 pipe, where it measured faster): interior tasks take a second body
 // (EDGE = false: the strip and its halo touch neither theta edge, 2 <= i0 and
 // i0 + W + 2 <= n_theta), with the periodic-wrap tests compiled out.
-template <typename T, int VEC, int TY, bool INIT, int D, bool EDGE, bool UNR = false>
+template <typename T, int VEC, int TY, bool INIT, int D, bool EDGE>
 __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Task &tk, int k,
                                                   T alpha, T *ring, T *yb, T *wb, int lane,
                                                   double (&out)[2])
@@ -1648,22 +1638,10 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
         hn_m1 = hn;
         he_m1 = he;
     };
-    if constexpr (UNR) {
-        // D + 1 steps per trip with the slots known at compile time (no slot
-        // arithmetic, and the rows carried in registers rotate without moves), then
-        // the 0..D rows left
-        int jr = tk.j0 - 1;
-        for (; jr + D <= tk.jend; jr += D + 1) {
-#pragma unroll
-            for (int u = 0; u <= D; ++u) step(jr + u, u);
-        }
-        for (int sl = 0; jr <= tk.jend; ++jr, ++sl) step(jr, sl);
-    } else {
-        int sl = 0;
-        for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
-            step(jr, sl);
-            sl = sl == D ? 0 : sl + 1;
-        }
+    int sl = 0;
+    for (int jr = tk.j0 - 1; jr <= tk.jend; ++jr) {
+        step(jr, sl);
+        sl = sl == D ? 0 : sl + 1;
     }
     cp_wait<0>();
     __syncwarp();
@@ -1671,7 +1649,7 @@ __device__ __forceinline__ void run_task_b_staged(const PcgDesc<T> &d, const Tas
     out[1] = arr.value();
 }
 
-template <typename T, int VEC, int TY, int MINB, bool INIT, int D, bool UNR = false, int NT = kThreads>
+template <typename T, int VEC, int TY, int MINB, bool INIT, int D, int NT = kThreads>
 __global__ void __launch_bounds__(NT, MINB) k_phase_b_staged(const PcgDesc<T> *__restrict__ dp)
 {
     using R = RingB<T, VEC>;
@@ -1700,9 +1678,9 @@ __global__ void __launch_bounds__(NT, MINB) k_phase_b_staged(const PcgDesc<T> *_
         double val[2];
         const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
         if (sizeof(T) == 8 && tk.i0 >= 2 && tk.i0 + W + 2 <= d.nth)
-            run_task_b_staged<T, VEC, TY, INIT, D, false, UNR>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
+            run_task_b_staged<T, VEC, TY, INIT, D, false>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
         else
-            run_task_b_staged<T, VEC, TY, INIT, D, true, UNR>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
+            run_task_b_staged<T, VEC, TY, INIT, D, true>(d, tk, s_k, (T)s_alpha, ring, yb, wb, lane, val);
         publish_unit<2>(val, reducer_of(d), ntasks, t, lane);
     }
     double tot[2];
