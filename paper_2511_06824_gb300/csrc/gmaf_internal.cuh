@@ -75,6 +75,10 @@ struct PcgDesc {
     double *partials;              // per-task (or per-warp) sums [ntiles][2], or per-block [2][grid]
     double *chunk_sum;             // two-level reduction: chunk sums [chunks][2] (nullptr: one level)
     unsigned *chunk_ctr;           // per-chunk counters, zero between launches
+    // block-marched phase B with TMA tiles (FP32): coefficient slots, task height and tasks
+    int nslots;                    // coefficient slots (planes of the coefficient maps)
+    int ty_b;                      // rows per task of that phase B
+    long long ntiles_b;            // its tasks
 };
 
 // FP64 residual r = S - A p over all conditions, with ||r||^2 and ||S||^2.
@@ -115,6 +119,7 @@ struct GraphCache {
     const void *ka = nullptr;      // phase kernels the graph was built with
     const void *kb = nullptr;
     int pairs = 0;                 // A -> B pairs per trip of the WHILE body
+    unsigned long long tma[12 * 16];   // tensor maps the phase-B nodes were given (or zero)
 };
 
 // Autotuner decision for one solve shape.
@@ -160,10 +165,12 @@ namespace gmaf {
 
 constexpr size_t kPinnedBytes = 64 * 1024;
 
-// Opt a kernel in to `bytes` of dynamic shared memory on the current device.
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device
+// (and, if asked, to the largest shared-memory carve-out).
 // The attribute is per device, so each call site keeps a mask of the device
 // ordinals it has set (ordinals from 64 on are set on every call).
-inline void smem_optin(std::atomic<unsigned long long> &done, const void *fn, size_t bytes)
+inline void smem_optin(std::atomic<unsigned long long> &done, const void *fn, size_t bytes,
+                       bool max_carveout = false)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -172,8 +179,14 @@ inline void smem_optin(std::atomic<unsigned long long> &done, const void *fn, si
     }
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (bit && (done.load() & bit)) return;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-        cudaSuccess)
+    bool ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+              cudaSuccess;
+    // the largest shared-memory carve-out, so that several blocks of a kernel with
+    // a large ring fit on one SM
+    if (ok && max_carveout)
+        ok = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+    if (ok)
         done.fetch_or(bit);
     else
         cudaGetLastError();

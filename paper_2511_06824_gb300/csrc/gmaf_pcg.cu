@@ -33,6 +33,7 @@
 #include "gmaf_pcg_kernels.cuh"
 #include "gmaf_pcg_host.cuh"
 #include "gmaf_mphase_kernels.cuh"
+#include "gmaf_tma.h"
 
 namespace gmaf {
 
@@ -113,10 +114,30 @@ static KernelSet<T> ks_staged_ab_nt(int rows = TY)
     return ks;
 }
 
-constexpr int kMaxVariants = 24;
+// Phase A staged two rows ahead (as ks_staged_ab, p updates paired) and the
+// block-marched TMA phase B with NS chunk slots, RPW rows per consumer warp
+// (chunks of 8 RPW rows; RPW 1: two blocks per SM, RPW 2: one) and tasks of
+// ty_b rows; id 3000000 + 10000 RPW + 1000 NS + ty_b.
+template <int NS, int RPW>
+static KernelSet<float> ks_tma(int ty_b)
+{
+    KernelSet<float> ks = ks_staged_ab<float, 4, 32, 2, 2>();
+    const TmaKernels tk = tma_kernels(NS, RPW);
+    ks.b = tk.b;
+    ks.b_init = tk.b_init;
+    ks.smem_b = tk.smem;
+    ks.tma = RPW;
+    ks.ty_b = ty_b;
+    ks.threads_b = kTmaThreads;
+    ks.id = 3000000 + 10000 * RPW + 1000 * NS + ty_b;
+    return ks;
+}
+
+constexpr int kMaxVariants = 28;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
-static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bool bulk_ok = false)
+static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bool bulk_ok = false,
+                    bool tma_ok = false)
 {
     int n = 0;
     if (vec_ok) {
@@ -142,10 +163,17 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bo
     out[n++] = ks_of<float, 1, 32, 4>(4);
     out[n++] = ks_of<float, 1, 16, 4>(5);
     out[n++] = ks_of<float, 1, 32, 4, 1>(0);
+    if (tma_ok) {
+        // block-marched TMA phase B; tasks of CR m - 2 rows fill whole chunks
+        out[n++] = ks_tma<4, 1>(62);
+        out[n++] = ks_tma<3, 2>(62);
+        out[n++] = ks_tma<4, 2>(62);
+        out[n++] = ks_tma<3, 2>(30);
+    }
     return n;
 }
 
-static int variants(KernelSet<double> *out, bool vec_ok, bool = false, bool = false)
+static int variants(KernelSet<double> *out, bool vec_ok, bool = false, bool = false, bool = false)
 {
     int n = 0;
     if (vec_ok) {
@@ -181,13 +209,40 @@ struct PcgRun {
     PcgDesc<T> h;
     KernelSet<T> ks;
     int grid_a, grid_b, grid_s;
+    TmaParams tma[2];       // tensor maps of the TMA phase B (FP32), chunks of 8 and 16 rows
+    bool tma_ready;         //   encoded for this run's arrays
 };
 
+// The tensor maps a kernel set's TMA phase B takes (chunks of 8 ks.tma rows).
+template <typename T>
+static const TmaParams *tma_params(const PcgRun<T> &run)
+{
+    return &run.tma[run.ks.tma > 1 ? 1 : 0];
+}
+
+// Launch a phase-B kernel of the run (the TMA kernels also take their maps).
+template <typename T>
+static cudaError_t launch_b(const PcgRun<T> &run, const void *fn, cudaStream_t s)
+{
+    const PcgDesc<T> *dd = run.d_desc;
+    void *args[] = {(void *)&dd, (void *)tma_params(run)};
+    return cudaLaunchKernel(fn, dim3(run.grid_b), dim3(b_threads(run.ks)), args, run.ks.smem_b, s);
+}
+
+// The phase-B nodes of a TMA kernel set carry the run's tensor maps; other sets none.
+template <typename T>
+static const void *graph_tma(const PcgRun<T> &run)
+{
+    static const unsigned long long none[12 * 16] = {};
+    return run.ks.tma ? (const void *)tma_params(run) : (const void *)none;
+}
+
 static bool graph_matches(const GraphCache &gc, int ga, int gb, int gs, const void *desc,
-                          const void *ka, const void *kb, int pairs)
+                          const void *ka, const void *kb, int pairs, const void *tma)
 {
     return gc.exec && gc.grid_a == ga && gc.grid_b == gb && gc.grid_s == gs && gc.desc == desc &&
-           gc.ka == ka && gc.kb == kb && gc.pairs == pairs;
+           gc.ka == ka && gc.kb == kb && gc.pairs == pairs &&
+           std::memcmp(gc.tma, tma, sizeof(gc.tma)) == 0;
 }
 
 // Build and instantiate  [init B] -> WHILE{A -> B} -> [finalize]  for a launch
@@ -206,15 +261,17 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
     cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0u, cudaGraphCondAssignDefault);
     const PcgDesc<T> *dd = run.d_desc;
     void *args[] = {(void *)&dd};
+    void *args_b[] = {(void *)&dd, (void *)tma_params(run)};   // the TMA kernels also take their maps
     cudaGraphNode_t n_init, n_while, n_fin, n_a, n_b;
     cudaKernelNodeParams kp{};
     kp.blockDim = dim3(kThreads);
     kp.kernelParams = args;
     if (e == cudaSuccess) {
-        kp.blockDim = dim3(run.ks.threads);
+        kp.blockDim = dim3(b_threads(run.ks));
         kp.func = (void *)run.ks.b_init;
         kp.gridDim = dim3(run.grid_b);
         kp.sharedMemBytes = (unsigned)run.ks.smem_b;
+        kp.kernelParams = run.ks.tma ? args_b : args;
         e = cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp);
     }
     cudaGraphNodeParams cp{};
@@ -231,13 +288,17 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
         cudaGraphNode_t prev = nullptr;
         for (int q = 0; q < pairs && e == cudaSuccess; ++q) {
             kp.func = (void *)run.ks.a;
+            kp.blockDim = dim3(run.ks.threads);
             kp.gridDim = dim3(run.grid_a);
             kp.sharedMemBytes = (unsigned)run.ks.smem_a;
+            kp.kernelParams = args;
             e = cudaGraphAddKernelNode(&n_a, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
             if (e == cudaSuccess) {
                 kp.func = (void *)run.ks.b;
+                kp.blockDim = dim3(b_threads(run.ks));
                 kp.gridDim = dim3(run.grid_b);
                 kp.sharedMemBytes = (unsigned)run.ks.smem_b;
+                kp.kernelParams = run.ks.tma ? args_b : args;
                 e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
             }
             prev = n_b;
@@ -245,6 +306,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
     }
     if (e == cudaSuccess) {
         kp.blockDim = dim3(kThreads);
+        kp.kernelParams = args;
         kp.func = (void *)k_finalize<T>;
         kp.gridDim = dim3(run.grid_s);
         kp.sharedMemBytes = 0;
@@ -264,6 +326,7 @@ static int build_graph(PcgRun<T> &run, GraphCache &gc, cudaStream_t s, int pairs
     gc.ka = run.ks.a;
     gc.kb = run.ks.b;
     gc.pairs = pairs;
+    std::memcpy(gc.tma, graph_tma(run), sizeof(gc.tma));
     (void)s;
     return GMAF_OK;
 }
@@ -299,6 +362,14 @@ static void shape_run(gmaf_ctx *ctx, PcgRun<T> &run, const KernelSet<T> &ks)
         run.grid_a = phase_grid(ks.a, h.ntiles, ctx->num_sms, ks.smem_a, ks.threads);
         run.grid_b = phase_grid(ks.b, h.ntiles, ctx->num_sms, ks.smem_b, ks.threads);
     }
+    h.ty_b = 0;
+    h.ntiles_b = 0;
+    if (ks.tma) {
+        // one block per task, tasks of ty_b rows
+        h.ty_b = ks.ty_b;
+        h.ntiles_b = (long long)h.tiles_x * ((h.nz + ks.ty_b - 1) / ks.ty_b) * h.K;
+        run.grid_b = grid_for(ks.b, h.ntiles_b, ctx->num_sms, ks.smem_b, b_threads(ks));
+    }
     run.grid_s = stream_grid(h.n * h.K, ctx->num_sms);
 }
 
@@ -306,6 +377,7 @@ template <typename T>
 static size_t partial_doubles(const PcgRun<T> &run)
 {
     long long m = 2 * run.h.ntiles;
+    if (2LL * run.h.ntiles_b > m) m = 2LL * run.h.ntiles_b;
     if (2LL * run.grid_s > m) m = 2LL * run.grid_s;
     // the static schedule publishes one partial pair per warp
     if (2LL * kWarps * run.grid_a > m) m = 2LL * kWarps * run.grid_a;
@@ -322,7 +394,8 @@ static size_t partial_doubles(const PcgRun<T> &run)
 template <typename T>
 static int attach_chunks(gmaf_ctx *ctx, PcgRun<T> &run)
 {
-    const long long units = run.ks.sched ? (long long)run.grid_a * kWarps : run.h.ntiles;
+    long long units = run.ks.sched ? (long long)run.grid_a * kWarps : run.h.ntiles;
+    if (run.h.ntiles_b > units) units = run.h.ntiles_b;
     run.h.chunk_sum = nullptr;
     run.h.chunk_ctr = nullptr;
     if (units < ctx->chunked_from) return GMAF_OK;
@@ -363,12 +436,12 @@ static int autotune(gmaf_ctx *ctx, PcgRun<T> &run, KernelSet<T> *cand, int ncand
             GMAF_CUDA(cudaMemcpyAsync(tr.d_desc, &tr.h, sizeof(PcgDesc<T>), cudaMemcpyHostToDevice, s));
             k_reset<<<1, 32, 0, s>>>(tr.h.sc, 0);
             k_init_r<T><<<tr.grid_s, kThreads, 0, s>>>(tr.d_desc);
-            GMAF_CUDA(launch<T>(tr.ks.b_init, tr.grid_b, tr.d_desc, s, tr.ks.smem_b, tr.ks.threads));
+            GMAF_CUDA(launch_b<T>(tr, tr.ks.b_init, s));
             const int warm = 3, reps = 10;
             for (int q = 0; q < warm + reps; ++q) {
                 if (q == warm) GMAF_CUDA(cudaEventRecord(ctx->ev[0], s));
                 GMAF_CUDA(launch<T>(tr.ks.a, tr.grid_a, tr.d_desc, s, tr.ks.smem_a, tr.ks.threads));
-                GMAF_CUDA(launch<T>(tr.ks.b, tr.grid_b, tr.d_desc, s, tr.ks.smem_b, tr.ks.threads));
+                GMAF_CUDA(launch_b<T>(tr, tr.ks.b, s));
             }
             GMAF_CUDA(cudaEventRecord(ctx->ev[1], s));
             GMAF_CUDA(cudaEventSynchronize(ctx->ev[1]));
@@ -395,7 +468,10 @@ static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
     run.d_desc = desc_slot;
     KernelSet<T> cand[kMaxVariants];
     const bool vo = vec_ok(h);
-    const int ncand = variants(cand, vo, vec8_ok(h), bulk_ok(h));
+    run.tma_ready = false;
+    if constexpr (sizeof(T) == 4)
+        run.tma_ready = vo && tma_encode_maps(h, run.tma[0], 8) && tma_encode_maps(h, run.tma[1], 16);
+    const int ncand = variants(cand, vo, vec8_ok(h), bulk_ok(h), run.tma_ready);
     int pick = 0;
     TuneEntry key{};
     key.tsize = (int)sizeof(T);
@@ -445,7 +521,7 @@ static int prepare(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc)
         run.h.use_cond = 0;
     } else {
         if (!graph_matches(gc, run.grid_a, run.grid_b, run.grid_s, run.d_desc, run.ks.a, run.ks.b,
-                           ctx->graph_pairs))
+                           ctx->graph_pairs, graph_tma(run)))
             GMAF_TRY(build_graph<T>(run, gc, ctx->stream, ctx->graph_pairs));
         run.h.use_cond = 1;
         run.h.cond = gc.handle;
@@ -518,7 +594,7 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
     int *it_h = (int *)ctx->pinned;        // iter, first, done of the scalars
     PhaseClock clk{ctx};
     clk.begin(s);
-    GMAF_CUDA(launch<T>(run.ks.b_init, run.grid_b, dd, s, run.ks.smem_b, run.ks.threads));
+    GMAF_CUDA(launch_b<T>(run, run.ks.b_init, s));
     clk.end(s, 2);
     const int chunk = 16;
     int prev_iter = -1;
@@ -534,7 +610,7 @@ static int pcg_once(gmaf_ctx *ctx, PcgRun<T> &run, GraphCache &gc, bool keep_ite
             GMAF_CUDA(launch<T>(run.ks.a, run.grid_a, dd, s, run.ks.smem_a, run.ks.threads));
             clk.end(s, 0);
             clk.begin(s);
-            GMAF_CUDA(launch<T>(run.ks.b, run.grid_b, dd, s, run.ks.smem_b, run.ks.threads));
+            GMAF_CUDA(launch_b<T>(run, run.ks.b, s));
             clk.end(s, 1);
         }
     }
@@ -950,6 +1026,7 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     h.r[1] = (float *)ctx->buf[B_R132];
     h.omega = (float)opts->omega;
     h.sc = dsc;
+    h.nslots = nslots;
     // The first outer residual and the inner right-hand side are formed before the
     // kernel set is chosen, so that the autotuner times iterations on real data.
     GMAF_TRY(ensure(ctx, B_PART, (size_t)2 * gs * sizeof(double)));

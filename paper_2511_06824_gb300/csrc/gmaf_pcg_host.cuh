@@ -52,7 +52,17 @@ struct KernelSet {
     size_t smem_a;             // dynamic shared memory of the phase-A kernel
     int p_period;              // iterations between two p updates of phase A (1 or 2)
     int threads = kThreads;    // threads per block of both phase kernels
+    int tma = 0;               // phase B is the block-marched TMA kernel (tasks per block)
+    int ty_b = 0;              //   its rows per task
+    int threads_b = 0;         // threads per block of the phase-B kernels (0: threads)
 };
+
+// Threads per block of a kernel set's phase-B kernels.
+template <typename T>
+static int b_threads(const KernelSet<T> &ks)
+{
+    return ks.threads_b ? ks.threads_b : ks.threads;
+}
 
 // id = 1000 VEC + 10 TY + MINB (dynamic), 1000000 + 1000 VEC + MINB (static).
 template <typename T, int VEC, int TY, int MINB, int SCHED = 0>
