@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--dyn-steps", type=int, default=36, help="shaft-angle steps (dynamics)")
     ap.add_argument("--kappa", type=float, default=None,
                     help="scale of the synthetic side load (dynamics; default: the calibrated value)")
+    ap.add_argument("--kinematics", choices=["fixed", "swash"], default="fixed",
+                    help="dynamics: the configured fixed gap length and 5 m/s sliding-speed "
+                         "amplitude (fixed), or the swash-plate piston of Table 8 (swash: gap "
+                         "length L_Fmin + R_b tan(beta) (1 - cos phi) and its rate)")
     ap.add_argument("--mass", type=float, default=None,
                     help="piston mass of the inertia load in kg (dynamics; default m_K of Table 8)")
     ap.add_argument("--scheme", choices=["general", "simplified", "both"], default="general",
@@ -548,11 +552,13 @@ def run_dynamics(args):
     schemes = ["general", "simplified"] if args.scheme == "both" else [args.scheme]
     kappa = DYN_KAPPA if args.kappa is None else args.kappa
     mass = dynamics.PISTON_MASS if args.mass is None else args.mass
+    kin = dynamics.SwashKinematics() if args.kinematics == "swash" else None
     runs = {}
     with gmaf.Context() as c:
         for scheme in schemes:
             dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof, 2, kappa=kappa,
-                           mass=mass, opts=gmaf.solver_opts(precision=prec), scheme=scheme)  # warm-up
+                           mass=mass, opts=gmaf.solver_opts(precision=prec), scheme=scheme,
+                           kinematics=kin)  # warm-up
             torch.cuda.synchronize()
             recs = []
             t0 = time.perf_counter()
@@ -561,7 +567,7 @@ def run_dynamics(args):
                 dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof,
                                args.dyn_steps, kappa=kappa, mass=mass,
                                opts=gmaf.solver_opts(precision=prec), on_step=recs.append,
-                               scheme=scheme)
+                               scheme=scheme, kinematics=kin)
             except gmaf.GmafError as ex:
                 failure = {"step": len(recs), "status": ex.status, "message": str(ex)}
             torch.cuda.synchronize()
@@ -588,7 +594,8 @@ def run_dynamics(args):
            "shaft_steps": args.dyn_steps, "scheme": schemes[0],
            "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
            "config": {"workload": wl, "joint_dof": w.dof, "steps_per_rev": 360,
-                      "warm_start": True, "kappa": kappa, "piston_mass_kg": mass, "tol_F": 1e-6}}
+                      "warm_start": True, "kappa": kappa, "piston_mass_kg": mass, "tol_F": 1e-6,
+                      "kinematics": args.kinematics}}
     out.update({k: v for k, v in head.items() if k not in ("value", "unit")})
     if len(schemes) > 1:
         out["schemes"] = runs

@@ -30,6 +30,18 @@ them only).  The march uses:
   about 1e-4 of the squeeze-film damping), so a converged step balances
   oil, side load and inertia exactly.
 
+Optionally (`kinematics=SwashKinematics()`) the piston moves as in a
+swash-plate pump with the geometry of Table 8 instead of the configured fixed gap
+length and sliding speed: the coupling length follows the piston stroke,
+L_F(phi) = L_Fmin + R_b tan(beta) (1 - cos phi) (L_Fmin at outer dead centre,
+phi = 0, growing by the stroke 2 R_b tan(beta) to inner dead centre), and the
+sliding speed is its rate, dL_F/dt = R_b omega tan(beta) sin(phi), with the sign
+convention of the configured v_amp sin(phi).  The paper gives Table 8's numbers
+but not these relations; they are the plain kinematics of a piston whose slipper
+follows a plane tilted by beta while the block turns at omega.  Each shaft step
+then solves on a gap of its own length (the grid keeps its cells), and the
+generalized coordinates stay the eccentricities at the two ends of the gap.
+
 Everything per Picard iteration runs on the device through the C ABI; this
 module is the host loop.  The pressure fields stay in the library's context and
 each solve warm-starts from the previous iterate (opts.zero_init = 0).
@@ -47,6 +59,30 @@ from . import gmaf
 
 SWASH_ANGLE_DEG = 10.0
 PISTON_MASS = 0.128          # m_K of Table 8 [kg]
+PITCH_RADIUS = 4.05e-2       # R_b of Table 8 [m]: radius of the pistons' pitch circle
+COUPLING_MIN = 3e-2          # L_Fmin of Table 8 [m]
+
+
+@dataclass(frozen=True)
+class SwashKinematics:
+    """Piston motion of a swash-plate pump: coupling length and sliding speed over
+    the shaft angle phi (0 at outer dead centre)."""
+    pitch_radius: float = PITCH_RADIUS
+    swash_deg: float = SWASH_ANGLE_DEG
+    coupling_min: float = COUPLING_MIN
+
+    @property
+    def stroke(self) -> float:
+        """Full piston stroke 2 R_b tan(beta)."""
+        return 2.0 * self.pitch_radius * math.tan(math.radians(self.swash_deg))
+
+    def coupling_length(self, phi: float) -> float:
+        """L_F(phi) = L_Fmin + R_b tan(beta) (1 - cos phi)."""
+        return self.coupling_min + 0.5 * self.stroke * (1.0 - math.cos(phi))
+
+    def sliding_speed(self, phi: float, rpm: float) -> float:
+        """dL_F/dt = R_b omega tan(beta) sin(phi), omega = 2 pi rpm / 60."""
+        return 0.5 * self.stroke * (2.0 * math.pi * rpm / 60.0) * math.sin(phi)
 
 
 def side_load(p_chamber: float, radius: float, kappa: float) -> np.ndarray:
@@ -101,6 +137,7 @@ class StepRecord:
     G_norm: float
     loads: np.ndarray
     seconds: float
+    gap_length: float = 0.0
 
 
 @dataclass
@@ -126,9 +163,12 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
           d_e: float = 2e-8, d_edot: float = 1e-6, opts: Optional[gmaf.gmaf_solver_opts] = None,
           on_step: Optional[Callable[[StepRecord], None]] = None,
           scheme: str = "general", mass: float = PISTON_MASS,
-          stepper: Optional[Callable] = None) -> Trajectory:
+          stepper: Optional[Callable] = None,
+          kinematics: Optional[SwashKinematics] = None) -> Trajectory:
     """Run `steps` shaft-angle steps.  p_profile[s % steps_per_rev] is the chamber
-    pressure of step s; the sliding speed is v_amp * sin(phi).
+    pressure of step s; the sliding speed is v_amp * sin(phi) and the gap length
+    phys[1], or, with `kinematics`, the swash-plate piston's speed and coupling
+    length at phi.
 
     scheme "general": the double-Jacobian Picard iteration (Eq. 2.12-2.19, 9 conditions).
     scheme "simplified": the conventional one (Eq. 2.20-2.22, 5 conditions); each time
@@ -154,6 +194,9 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
         ph = phys.copy()
         ph[5] = float(p_profile[s % steps_per_rev])
         ph[4] = v_amp * math.sin(phi)
+        if kinematics is not None:
+            ph[1] = kinematics.coupling_length(phi)
+            ph[4] = kinematics.sliding_speed(phi, rpm)
         F_side = side_load(ph[5], ph[0], kappa)
         scale = force_scale(F_side, ph[5], ph[0])
         e_prev = state[:4].copy()
@@ -180,7 +223,7 @@ def march(ctx: int, n_theta: int, n_z: int, phys, tex, state0, p_profile, steps:
         rec = StepRecord(step=s, phi_deg=math.degrees(phi), p_chamber=ph[5], v_slide=ph[4],
                          picard_iterations=it, pcg_iterations=pcg, converged=converged,
                          state=state.copy(), G_norm=G_norm, loads=loads.copy(),
-                         seconds=time.perf_counter() - t0)
+                         seconds=time.perf_counter() - t0, gap_length=float(ph[1]))
         traj.records.append(rec)
         if on_step:
             on_step(rec)

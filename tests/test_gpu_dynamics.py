@@ -23,10 +23,12 @@ def g():
 
 
 def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, max_picard=20,
-                 mass=0.128):
+                 mass=0.128, swash=False):
     """The march with the oracle's Picard step: side load on e3, and the inertia of a
     piston of `mass` spread evenly over the gap, -M (edot - edot_l) / dt with
-    M = mass / 6 [[2, 1], [1, 2]] on (e1, e3) and on (e2, e4)."""
+    M = mass / 6 [[2, 1], [1, 2]] on (e1, e3) and on (e2, e4).  swash: the gap length
+    and sliding speed of the swash-plate piston of Table 8 (R_b = 40.5 mm, 10 degrees,
+    L_Fmin = 30 mm, 600 rpm), L_Fmin + R_b tan(10 deg) (1 - cos phi) and its rate."""
     dt = (60.0 / 600.0) / 360.0
     M = mass / 6.0 * np.array([[2, 0, 1, 0], [0, 2, 0, 1], [1, 0, 2, 0], [0, 1, 0, 2.0]])
     out = []
@@ -35,6 +37,10 @@ def oracle_march(nth, nz, phys, tex, st, prof, steps, kappa, eps, tol_F=1e-6, ma
         ph = phys.copy()
         ph[5] = prof[s % 360]
         ph[4] = 5.0 * math.sin(phi)
+        if swash:
+            rt = 4.05e-2 * math.tan(math.radians(10.0))
+            ph[1] = 3e-2 + rt * (1 - math.cos(phi))
+            ph[4] = rt * (2 * math.pi * 600 / 60) * math.sin(phi)
         f = kappa * ph[5] * math.pi * ph[0] ** 2 * math.tan(math.radians(10.0))
         F = np.array([0.0, 0.0, f, 0.0])
         e_prev = st[:4].copy()
@@ -69,6 +75,33 @@ def test_march_matches_oracle(g, precision, tol, mass):
     ref = oracle_march(nth, nz, phys, tex, st0.copy(), prof, steps, 0.2, eps, mass=mass)
     got = traj.states
     assert all(r.converged for r in traj.records)
+    scale = np.abs(ref[:, :4]).max()
+    assert np.max(np.abs(got[:, :4] - ref[:, :4])) <= tol * scale
+    rscale = np.abs(ref[:, 4:]).max()
+    assert np.max(np.abs(got[:, 4:] - ref[:, 4:])) <= 10 * tol * rscale
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-6), (1, 1e-4)])
+def test_swash_kinematics_march_matches_oracle(g, precision, tol):
+    """With the swash-plate kinematics every shaft step solves on a gap of its own
+    length (30 mm at outer dead centre, growing with the stroke) at the piston's
+    speed; the warm-started solves carry the previous step's fields across the change
+    of gap length."""
+    from paper_2511_06824_gb300 import dynamics
+    nth, nz, steps = 48, 24, 10
+    phys = inputs.phys_vector()
+    tex = inputs.dimple_texture(np.random.default_rng(4))
+    prof = inputs.trapezoid_pressure_profile(np.random.default_rng(3), 360)
+    st0 = np.array([2e-6, -1e-6, 3e-6, 1e-6, 0, 0, 0, 0.0])
+    eps = 1e-12
+    with g.Context() as c:
+        traj = dynamics.march(c.handle, nth, nz, phys, tex, st0, prof, steps, kappa=0.2,
+                              opts=g.solver_opts(eps=eps, precision=precision),
+                              kinematics=dynamics.SwashKinematics())
+    ref = oracle_march(nth, nz, phys, tex, st0.copy(), prof, steps, 0.2, eps, swash=True)
+    assert all(r.converged for r in traj.records)
+    assert traj.records[0].gap_length == 3e-2 and traj.records[-1].gap_length > 3e-2
+    got = traj.states
     scale = np.abs(ref[:, :4]).max()
     assert np.max(np.abs(got[:, :4] - ref[:, :4])) <= tol * scale
     rscale = np.abs(ref[:, 4:]).max()
