@@ -127,3 +127,55 @@ def test_tma_phase_b_two_level_reduction(g, monkeypatch):
     so, D, aE, aN, S = arrs
     sto, po, ito, _, _ = oracle.solve_joint(nth, nz, D, aE, aN, S, precond=1, omega=1.2, eps=1e-10)
     assert rel_l2(two[0], po) <= 1e-6
+
+
+def load_err(a, b):
+    """Relative load error per component, forces and moments each against
+    max(|F_c|, 1e-3 ||F||)."""
+    a, b = np.asarray(a), np.asarray(b)
+    out = 0.0
+    for part in (slice(0, 6), slice(6, 12)):
+        x, y = a[..., part], b[..., part]
+        nrm = np.linalg.norm(y, axis=-1, keepdims=True)
+        out = max(out, float(np.max(np.abs(x - y) / np.maximum(np.abs(y), 1e-3 * nrm))))
+    return out
+
+
+@pytest.mark.parametrize("variant,scheme", [(3014062, "general"), (3023062, "general"),
+                                            (3014062, "simplified")])
+def test_tma_phase_b_picard_step_matches_oracle(g, monkeypatch, variant, scheme):
+    """The Picard step stores 5 coefficient slots for its 9 conditions (the simplified
+    scheme one for its 5), so each task's coefficient copies come from the slot of its
+    condition: loads, G, Jacobian and update against the oracle's step, mixed
+    precision."""
+    monkeypatch.setenv("GMAF_VARIANT", str(variant))
+    nth, nz = 256, 128
+    tex = inputs.dimple_texture(np.random.default_rng(5))
+    st0 = inputs.random_state(np.random.default_rng(31))
+    e_prev = st0[:4] - 2e-8
+    F = np.array([25.0, -10.0, 4.0, 3.0])
+    dt, eps = 2.78e-4, 1e-12
+    c = g.Context()
+    try:
+        if scheme == "general":
+            r = g.gmaf_picard_step(c.handle, nth, nz, PHYS, tex, st0, e_prev, dt, F, 2e-8, 1e-6,
+                                   g.solver_opts(eps=eps, precision=1))
+        else:
+            r = g.gmaf_picard_step_simplified(c.handle, nth, nz, PHYS, tex, st0, dt, F, 1e-6,
+                                              g.solver_opts(eps=eps, precision=1))
+        info = g.gmaf_last_solve_info(c.handle)
+    finally:
+        c.close()
+    if scheme == "general":
+        o = oracle.picard_step(nth, nz, PHYS, tex, st0, e_prev, dt, F, 2e-8, 1e-6, eps=eps)
+        Jg, Jo = r["J"], o["J"]
+    else:
+        o = oracle.picard_step_simplified(nth, nz, PHYS, tex, st0, dt, F, 1e-6, eps=eps)
+        Jg, Jo = r["J"][:, 4:], o["J"][:, 4:]
+    assert info["kernel_variant"] == variant
+    assert r["status"] == 0 and o["status"] == 0
+    assert load_err(r["loads"], o["loads"]) <= 1e-5
+    assert np.max(np.abs(Jg - Jo) / np.abs(Jo).max(axis=0, keepdims=True)) <= 1e-3
+    np.testing.assert_allclose(r["G"], o["G"], rtol=1e-6, atol=1e-6 * np.abs(o["G"]).max())
+    ds_g, ds_o = r["state"] - st0, o["state"] - st0
+    assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o) + 1e-20
