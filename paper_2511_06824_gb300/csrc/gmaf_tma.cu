@@ -84,15 +84,18 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 // Bounded wait for the phase of `parity`, sleeping NS_SLEEP nanoseconds between
 // polls so that a waiting lane takes few issue slots from the working warps:
-// false after about two seconds (or 2^22 polls), true once the phase completed.
+// false after about two seconds (or 2^22 polls), or as soon as *stop is set,
+// true once the phase completed.
 template <unsigned NS_SLEEP>
-__device__ __forceinline__ bool mbar_wait_nap(unsigned long long *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait_nap(unsigned long long *bar, unsigned parity,
+                                              const int *stop = nullptr)
 {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned k = 0; k < kBarSpin; ++k) {
         __nanosleep(NS_SLEEP);
         if (mbar_test(bar, parity)) return true;
+        if (stop && *(const volatile int *)stop) return false;
         if (global_ns() - t0 > 2000000000ull) return false;
     }
     return false;
@@ -298,7 +301,7 @@ __global__ void __maxnreg__(RPW == 1 ? 96 : 168) k_phase_b_tma(const PcgDesc<flo
             if (lane == 0) {
                 const int slot = (int)(g % NS);
                 // the consumers release a slot once its chunk has been read
-                if (g >= NS && !mbar_wait_nap<256>(&s_empty[slot], ((g / NS) - 1u) & 1u)) go = 0;
+                if (g >= NS && !mbar_wait_nap<256>(&s_empty[slot], ((g / NS) - 1u) & 1u, &s_abort)) go = 0;
                 if (go && *(volatile int *)&s_abort) go = 0;
                 if (!go) {
                     if (atomicExch(&s_abort, 1) == 0) {
@@ -337,6 +340,7 @@ __global__ void __maxnreg__(RPW == 1 ? 96 : 168) k_phase_b_tma(const PcgDesc<flo
         size_t base = 0;                     // cond * n + i0 + 4 lane
         bool at_w = false, at_e = false;     // the lane holds column 0 / column n_theta - 1
         RowAcc<float> arz, arr;
+        bool lost = false;                   // thread 0: a task's sums could not be handed over
         TmaKept kept[RPW];
 #pragma unroll
         for (int i = 0; i < RPW; ++i) {
@@ -447,7 +451,7 @@ __global__ void __maxnreg__(RPW == 1 ? 96 : 168) k_phase_b_tma(const PcgDesc<flo
                     for (int q = 0; q < 4; ++q) r1[i][q] = y[i][q] = od[i][q] = an[i][q] = 0.0f;
                 }
             }
-            if (!consumers_sync_and(ok != 0)) {
+            if (!consumers_sync_and(ok != 0 && !lost)) {
                 // a wait gave up: the producer warp drains and publishes after the loop
                 if (threadIdx.x == 0) {
                     s_consumed = g;
@@ -560,7 +564,10 @@ __global__ void __maxnreg__(RPW == 1 ? 96 : 168) k_phase_b_tma(const PcgDesc<flo
                         sb += s_red[w2][1];
                     }
                     const unsigned tail = s_mb.tail;
-                    // a free entry (the producer publishes between its copies; bounded)
+                    // a free entry: at most NS + 1 tasks wait in the mailbox (the producer
+                    // publishes after every copy it issues and the consumers cannot run
+                    // more than NS chunks ahead of it), so one is free unless the producer
+                    // stopped; the wait is bounded all the same
                     unsigned spin = 0;
                     while (tail - *(volatile unsigned *)&s_mb.head >= (unsigned)kTmaMail && spin < kBarSpin) {
                         __nanosleep(64);
@@ -573,9 +580,15 @@ __global__ void __maxnreg__(RPW == 1 ? 96 : 168) k_phase_b_tma(const PcgDesc<flo
                         s_mb.v[e][1] = sb;
                         __threadfence_block();
                         *(volatile unsigned *)&s_mb.tail = tail + 1u;
-                    } else if (atomicExch(&s_abort, 1) == 0) {
-                        sc->status = GMAF_TIMEOUT;
-                        __threadfence();
+                    } else {
+                        // not handed over: the consumers stop at the next chunk, before
+                        // any later task, so the cleanup below finds this one among the
+                        // claimed tasks not published and publishes zero sums for it
+                        lost = true;
+                        if (atomicExch(&s_abort, 1) == 0) {
+                            sc->status = GMAF_TIMEOUT;
+                            __threadfence();
+                        }
                     }
                 }
             }
