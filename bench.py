@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="step mode: skip the short serving sample of the bench line")
+    ap.add_argument("--no-dynamics", action="store_true",
+                    help="step mode: skip the short multi-period march of the bench line")
     ap.add_argument("--mode", choices=["step", "dynamics", "serving", "strategies", "precond"],
                     default="step",
                     help="step: Picard steps of the joint batch (default); dynamics: the "
@@ -437,12 +441,98 @@ def run_ours(args):
                        "note": "FP64 mode is bound by GB300's FP64 pipe, not by HBM"}
     ctx.close()
 
+    if rank == 0 and world == 1 and not args.no_serving:
+        out["serving"] = guarded(serving_sample, args)
+    if rank == 0 and world == 1 and not args.no_dynamics:
+        out["dynamics"] = guarded(dynamics_sample, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=25.0)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def guarded(fn, args):
+    """A side measurement of the bench line: its result, or the error it raised (the
+    headline stands either way)."""
+    try:
+        return fn(args)
+    except Exception as ex:           # noqa: BLE001 - reported in the line, not hidden
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
+SAMPLE_REQUESTS = 8                   # serving sample of the bench line
+SAMPLE_EPS_SERVED = 1e-9              # eps of each side at equal load accuracy (<= 1e-5 against
+SAMPLE_EPS_SEQUENTIAL = 3e-10         #   the FP64 reference), from bench.py --mode serving
+SAMPLE_SHAFT_STEPS = 36               # dynamics sample of the bench line: a tenth of a revolution
+
+
+def serving_sample(args):
+    """A short served stream (Poisson arrivals at --rate, grids over 256x128 .. 2048x1024,
+    half textured): the continuous-batching mixed-precision server at the stream's
+    rate and all at once, against the sequential one-system-at-a-time FP64 baseline
+    all at once, each at the eps that `--mode serving` calibrates for equal load
+    accuracy.  Reports Picard steps/s and p50/p99 step latency."""
+    import torch
+    from paper_2511_06824_gb300 import gmaf, inputs, serving
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = inputs.serving_requests(seed=args.seed, count=SAMPLE_REQUESTS, rate_hz=args.rate)
+    items = serving.items_from_requests(reqs)
+    budget = int(args.budget_gb * (1 << 30))
+    with gmaf.Context() as c:
+        warm = serving.items_from_requests(inputs.serving_requests(seed=999, count=2, rate_hz=1e6,
+                                                                   grids=[(256, 128)]))
+        serving.serve_stream(c.handle, warm, 2 << 30, eps=1e-10)      # load kernels
+        serving.sequential_stream(c.handle, warm[:1], eps=1e-10)
+        at_rate = serving.serve_stream(c.handle, items, budget, eps=SAMPLE_EPS_SERVED, round_iters=64)
+        sat = serving.serve_stream(c.handle, items, budget, eps=SAMPLE_EPS_SERVED, round_iters=64,
+                                   time_scale=0.0)
+        seq = serving.sequential_stream(c.handle, items, eps=SAMPLE_EPS_SEQUENTIAL, time_scale=0.0)
+    diff = max(serving.load_error(a["loads"], b["loads"])
+               for a, b in zip(sat["results"], seq["results"]))
+    keep = ("picard_steps_per_s", "p50_ms", "p99_ms", "max_active")
+    return {"metric": "Picard steps/s and p50/p99 step ms (served stream)",
+            "served_at_stream_rate": {k: at_rate[k] for k in keep},
+            "served_all_at_once": {k: sat[k] for k in keep},
+            "sequential_fp64_all_at_once": {"picard_steps_per_s": seq["picard_steps_per_s"]},
+            "speedup_at_saturation": sat["picard_steps_per_s"] / seq["picard_steps_per_s"],
+            "max_load_difference_served_vs_sequential": diff,
+            "config": {"requests": SAMPLE_REQUESTS, "rate_hz": args.rate, "seed": args.seed,
+                       "grids": [list(x) for x in inputs.SERVING_GRIDS], "textured_fraction": 0.5,
+                       "budget_gb": args.budget_gb, "served_eps": SAMPLE_EPS_SERVED,
+                       "sequential_eps": SAMPLE_EPS_SEQUENTIAL, "round_iters": 64}}
+
+
+def dynamics_sample(args):
+    """A tenth of a revolution of the multi-period march (textured 1024x512 x 9, mixed,
+    360 shaft steps per revolution, warm-started, calibrated side load and piston
+    inertia): Picard steps/s and Picard iterations per shaft step."""
+    import torch
+    from paper_2511_06824_gb300 import dynamics, gmaf, inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl = "textured-1024x512-k9"
+    w = inputs.make(wl, args.seed)
+    prof = inputs.trapezoid_pressure_profile(np.random.default_rng(args.seed + 100), 360)
+    st0 = np.concatenate([w.state[:4] * 0.2, np.zeros(4)])
+    with gmaf.Context() as c:
+        o = gmaf.solver_opts(precision=1)
+        dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof, 2, kappa=DYN_KAPPA,
+                       opts=o)                                          # tuning and warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        traj = dynamics.march(c.handle, w.n_theta, w.n_z, w.phys, w.tex, st0, prof,
+                              SAMPLE_SHAFT_STEPS, kappa=DYN_KAPPA, opts=o)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    pic = traj.picard_iterations
+    return {"metric": "Picard steps/s (multi-period march)", "value": pic / dt,
+            "unit": "Picard steps/s", "shaft_steps": SAMPLE_SHAFT_STEPS,
+            "s_per_shaft_step": dt / SAMPLE_SHAFT_STEPS,
+            "picard_per_shaft_step": pic / SAMPLE_SHAFT_STEPS,
+            "converged_steps": sum(r.converged for r in traj.records),
+            "config": {"workload": wl, "steps_per_rev": 360, "kappa": DYN_KAPPA,
+                       "piston_mass_kg": dynamics.PISTON_MASS, "tol_F": 1e-6, "precision": "mixed"}}
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)
