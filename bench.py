@@ -107,7 +107,8 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def alg_bytes_per_dof(precision: str, n_cond: int = 9, n_slots: int = 5, p_period: int = 1):
+def alg_bytes_per_dof(precision: str, n_cond: int = 9, n_slots: int = 5, p_period: int = 1,
+                      diag_rebuilt: bool = False):
     """Algorithmic bytes per joint DOF per launch of each PCG phase, averaged over
     iterations.
 
@@ -117,11 +118,18 @@ def alg_bytes_per_dof(precision: str, n_cond: int = 9, n_slots: int = 5, p_perio
     writes r, z.  Each phase reads three coefficient arrays (D, a_E, a_N in A;
     1/D, a_E, a_N in B), stored once per coefficient slot: 5 slots serve the 9
     conditions because the rate-perturbed conditions share the matrix of the base
-    condition."""
+    condition.  diag_rebuilt: phase A forms D from a_E and a_N and reads only the
+    Dirichlet term of the first and last rows (2 / n_z of an array, left out)."""
     w = 4 if precision == "mixed" else 8
-    coef = 3 * w * n_slots / n_cond
+    coef = w * n_slots / n_cond
     p_bytes = 2 * w if p_period == 1 else 3 * w / 2
-    return {"phase_a": 4 * w + p_bytes + coef, "phase_b": 4 * w + coef}
+    return {"phase_a": 4 * w + p_bytes + (2 if diag_rebuilt else 3) * coef,
+            "phase_b": 4 * w + 3 * coef}
+
+
+def diag_rebuilt(variant: int) -> bool:
+    """Whether a kernel variant's phase A rebuilds the diagonal (id + 10000000)."""
+    return (int(variant) // 10000000) % 10 == 1
 
 
 class ClockSampler:
@@ -366,7 +374,8 @@ def run_ours(args):
     ph = gmaf.gmaf_phase_timing(ctx.handle)
     gmaf.gmaf_set_phase_timing(ctx.handle, False)
     hbm, peak_kind = peaks()
-    bpd = alg_bytes_per_dof(args.precision, p_period=timed.info.get("p_update_period", 1))
+    bpd = alg_bytes_per_dof(args.precision, p_period=timed.info.get("p_update_period", 1),
+                            diag_rebuilt=diag_rebuilt(timed.info["kernel_variant"]))
     phases = {}
     for k in ("phase_a", "phase_b"):
         tot, cnt = ph[k]

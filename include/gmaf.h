@@ -120,9 +120,14 @@ typedef struct {
     int32_t kernel_variant;    /* PCG kernels used: 1000 VEC + 10 TY + MINB (columns per
                                   lane, rows per task, blocks per SM), + 100000 DB when
                                   phase B stages its rows DB ahead through shared memory,
-                                  + 200000 DA when phase A does; 1000000 + 1000 VEC + MINB
-                                  for the static schedule.  Chosen per problem shape by
-                                  the autotuner on the first solve of that shape */
+                                  + 200000 DA when phase A does, + 2000000 when phase B
+                                  is filled by bulk copies, + 10000000 when phase A
+                                  rebuilds the diagonal from the couplings, + 100000000 W
+                                  for blocks of W warps; 1000000 + 1000 VEC + MINB for the
+                                  static schedule; 3000000 + 10000 RPW + 1000 NS + TB for
+                                  the block-marched phase B with TMA tiles.  Chosen per
+                                  problem shape by the autotuner on the first solve of
+                                  that shape */
     int32_t tasks;             /* strip x row-block x condition tasks per PCG phase       */
     int32_t iterations_sum;    /* PCG iterations summed over the conditions: n_cond x
                                   iterations under the synchronized criterion, the sum of

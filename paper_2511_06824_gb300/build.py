@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgmaf.so")
-SOURCES = ["gmaf_api.cu", "gmaf_assemble.cu", "gmaf_pcg.cu", "gmaf_tma.cu", "gmaf_server.cu",
-           "gmaf_noalloc.cu"]
+SOURCES = ["gmaf_api.cu", "gmaf_assemble.cu", "gmaf_pcg.cu", "gmaf_tma.cu", "gmaf_drec.cu",
+           "gmaf_server.cu", "gmaf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

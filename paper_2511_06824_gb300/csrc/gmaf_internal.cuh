@@ -77,6 +77,8 @@ struct PcgDesc {
     unsigned *chunk_ctr;           // per-chunk counters, zero between launches
     // block-marched phase B with TMA tiles (FP32): coefficient slots, task height and tasks
     int nslots;                    // coefficient slots (planes of the coefficient maps)
+    const T *dbnd;                 // phase A with the rebuilt diagonal: the Dirichlet term of
+                                   // the first and last rows, [slots][2][n_theta] (or null)
     int ty_b;                      // rows per task of that phase B
     long long ntiles_b;            // its tasks
 };
@@ -108,6 +110,8 @@ enum BufId {
     B_ASYNC,
     // two-level reduction of the phase kernels: chunk sums, chunk counters
     B_CHUNK, B_CHUNKCTR,
+    // boundary rows' Dirichlet term of the FP32 diagonal (phase A with the rebuilt diagonal)
+    B_DBND32,
     B_COUNT
 };
 

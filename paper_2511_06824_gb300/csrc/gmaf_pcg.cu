@@ -34,6 +34,7 @@
 #include "gmaf_pcg_host.cuh"
 #include "gmaf_mphase_kernels.cuh"
 #include "gmaf_tma.h"
+#include "gmaf_drec.h"
 
 namespace gmaf {
 
@@ -133,11 +134,23 @@ static KernelSet<float> ks_tma(int ty_b)
     return ks;
 }
 
+// ks_staged_ab<float, 4, 32, 2, 2> with phase A rebuilding the diagonal from the
+// couplings (gmaf_drec.cu); id + 10000000.
+static KernelSet<float> ks_drec()
+{
+    KernelSet<float> ks = ks_staged_ab<float, 4, 32, 2, 2>();
+    const DrecKernel dk = drec_phase_a();
+    ks.a = dk.a;
+    ks.smem_a = dk.smem;
+    ks.id += 10000000;
+    return ks;
+}
+
 constexpr int kMaxVariants = 28;
 
 // Candidate variants; the vector ones need n_theta % VEC == 0 and aligned fields.
 static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bool bulk_ok = false,
-                    bool tma_ok = false)
+                    bool tma_ok = false, bool drec_ok = false)
 {
     int n = 0;
     if (vec_ok) {
@@ -145,6 +158,7 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bo
         // schedule keep every warp busy on smaller ones (1024 x 512 x 9 has only
         // 1152 tasks of 32 rows for 2432 resident warps)
         out[n++] = ks_staged_ab<float, 4, 32, 2, 2>();
+        if (drec_ok) out[n++] = ks_drec();
         // 3 blocks of 6 warps per SM (18 warps, 94 registers); the task height is a
         // run-time choice: with equal tasks the phase lasts whole waves of tasks, and
         // on 2048 x 1024 x 9 18-row tasks fill exactly 3 waves of the 2736 warps
@@ -173,7 +187,8 @@ static int variants(KernelSet<float> *out, bool vec_ok, bool vec8_ok = false, bo
     return n;
 }
 
-static int variants(KernelSet<double> *out, bool vec_ok, bool = false, bool = false, bool = false)
+static int variants(KernelSet<double> *out, bool vec_ok, bool = false, bool = false, bool = false,
+                    bool = false)
 {
     int n = 0;
     if (vec_ok) {
@@ -211,6 +226,7 @@ struct PcgRun {
     int grid_a, grid_b, grid_s;
     TmaParams tma[2];       // tensor maps of the TMA phase B (FP32), chunks of 8 and 16 rows
     bool tma_ready;         //   encoded for this run's arrays
+    bool drec_ready;        // h.dbnd holds the boundary term of the rebuilt diagonal (FP32)
 };
 
 // The tensor maps a kernel set's TMA phase B takes (chunks of 8 ks.tma rows).
@@ -471,7 +487,7 @@ static int setup_run(gmaf_ctx *ctx, PcgRun<T> &run, PcgDesc<T> *desc_slot)
     run.tma_ready = false;
     if constexpr (sizeof(T) == 4)
         run.tma_ready = vo && tma_encode_maps(h, run.tma[0], 8) && tma_encode_maps(h, run.tma[1], 16);
-    const int ncand = variants(cand, vo, vec8_ok(h), bulk_ok(h), run.tma_ready);
+    const int ncand = variants(cand, vo, vec8_ok(h), bulk_ok(h), run.tma_ready, run.drec_ready);
     int pick = 0;
     TuneEntry key{};
     key.tsize = (int)sizeof(T);
@@ -1027,6 +1043,14 @@ int solve_joint_device(gmaf_ctx *ctx, int nth, int nz, int K, int nslots, const 
     h.omega = (float)opts->omega;
     h.sc = dsc;
     h.nslots = nslots;
+    if (nth % 4 == 0) {
+        // the boundary term of the diagonal for the phase A variant that rebuilds it
+        GMAF_TRY(ensure(ctx, B_DBND32, (size_t)nslots * 2 * nth * sizeof(float)));
+        GMAF_TRY(launch_dbnd32(h.D, h.aE, h.aN, (float *)ctx->buf[B_DBND32], nth, nz, nslots,
+                               ctx->num_sms, s));
+        h.dbnd = (const float *)ctx->buf[B_DBND32];
+        run.drec_ready = true;
+    }
     // The first outer residual and the inner right-hand side are formed before the
     // kernel set is chosen, so that the autotuner times iterations on real data.
     GMAF_TRY(ensure(ctx, B_PART, (size_t)2 * gs * sizeof(double)));

@@ -1244,7 +1244,11 @@ struct RingA {
     __host__ __device__ static constexpr int per_warp(int D) { return (D + 1) * NF * NB + 2 * NB; }
 };
 
-template <typename T, int VEC, int TY, int D, bool PAIR = false>
+// DREC: the diagonal is not staged but rebuilt from the couplings the row step
+// already holds, D = aE + aW + aN + aS (+ the Dirichlet term of the first and last
+// rows, read from d.dbnd), as the assembly forms it; 4 bytes fewer per unknown and
+// coefficient slot.
+template <typename T, int VEC, int TY, int D, bool PAIR = false, bool DREC = false>
 __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const Task &tk, int k,
                                                     int first, int pend, T alpha_prev, T alpha_pp,
                                                     T beta, T *ring, T *ub, T *ab, int lane)
@@ -1289,6 +1293,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             for (int f = 0; f < NF; ++f) {
                 if ((uz && f == 1) || (nop && f == 5)) continue;     // no u' / no p update
                 if (f == 6 && !two) continue;
+                if (DREC && f == 2) continue;                        // D rebuilt, not copied
                 if (!in && (f == 2 || f == 3 || f >= 5)) continue;
                 if (!owned && f >= 5) continue;
 #pragma unroll
@@ -1327,7 +1332,7 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
             if (!uz) Vec<T, VEC>::ldrw(cur + NB + sown, uov);
             Vec<T, VEC>::ldrw(cur + 4 * NB + sown, nv);
             if (in) {
-                Vec<T, VEC>::ldrw(cur + 2 * NB + sown, Dv);
+                if constexpr (!DREC) Vec<T, VEC>::ldrw(cur + 2 * NB + sown, Dv);
                 Vec<T, VEC>::ldrw(cur + 3 * NB + sown, ev);
                 if (!nop) Vec<T, VEC>::ldrw(cur + 5 * NB + sown, pv);
                 if (two) Vec<T, VEC>::ldrw(cur + 6 * NB + sown, uppv);
@@ -1344,13 +1349,27 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
         if (jo >= tk.j0 && jo < tk.jend) {
             T vout[VEC];
             T rowsum = T(0);
+            T bnd[VEC];
+            if constexpr (DREC) {
+                // Dirichlet term of the first and last rows: d.dbnd[slot][0 or 1][n_theta]
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) bnd[q] = T(0);
+                if (jo == 0 || jo == nz - 1)
+                    Vec<T, VEC>::ld(d.dbnd + ((size_t)d.cslot[tk.cond] * 2 + (jo == 0 ? 0 : 1)) * nth + g0,
+                                    bnd);
+            }
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
                 const int s = sown + q;
                 const T uE = (q < VEC - 1) ? u_m1[q + 1] : ub[s + 1];
                 const T uW = (q > 0) ? u_m1[q - 1] : ub[s - 1];
                 const T aW = (q > 0) ? e_m1[q - 1] : ab[s - 1];
-                vout[q] = D_m1[q] * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
+                T dg;
+                if constexpr (DREC)
+                    dg = (((e_m1[q] + aW) + n_m1[q]) + n_m2[q]) + bnd[q];
+                else
+                    dg = D_m1[q];
+                vout[q] = dg * u_m1[q] - e_m1[q] * uE - aW * uW - n_m1[q] * u[q] -
                           n_m2[q] * u_m2[q];
                 rowsum += u_m1[q] * vout[q];
             }
@@ -1398,7 +1417,8 @@ __device__ __forceinline__ double run_task_a_staged(const PcgDesc<T> &d, const T
 }
 
 // FP32: the p updates are paired (PAIR above); FP64 adds one every iteration.
-template <typename T, int VEC, int TY, int MINB, int D, int NT = kThreads>
+// DREC: the diagonal rebuilt from the couplings (run_task_a_staged).
+template <typename T, int VEC, int TY, int MINB, int D, int NT = kThreads, bool DREC = false>
 __global__ void __launch_bounds__(NT, MINB) k_phase_a_staged(const PcgDesc<T> *__restrict__ dp)
 {
     constexpr bool PAIR = sizeof(T) == 4;
@@ -1436,7 +1456,7 @@ __global__ void __launch_bounds__(NT, MINB) k_phase_a_staged(const PcgDesc<T> *_
     for (unsigned t = next_task(&sc->task_ctr[0], lane); t < ntasks;
          t = next_task(&sc->task_ctr[0], lane)) {
         const Task tk = task_of_rows<W>(t, d.K, d.tiles_x, d.nz, d.ty > 0 ? d.ty : TY);
-        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR>(
+        const double val[1] = {run_task_a_staged<T, VEC, TY, D, PAIR, DREC>(
             d, tk, s_k, s_first, s_pend, (T)s_alpha, (T)s_alpha_pp, (T)s_beta, ring, ub, ab, lane)};
         publish_unit<1>(val, reducer_of(d), ntasks, t, lane);
     }

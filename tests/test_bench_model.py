@@ -21,3 +21,12 @@ def test_paired_p_updates_save_two_bytes_per_unknown_in_fp32():
     two = bench.alg_bytes_per_dof("mixed", p_period=2)
     assert one["phase_a"] - two["phase_a"] == pytest.approx(2.0)
     assert one["phase_b"] == two["phase_b"]
+
+
+def test_rebuilt_diagonal_drops_one_coefficient_array_from_phase_a():
+    base = bench.alg_bytes_per_dof("mixed", p_period=2)
+    drec = bench.alg_bytes_per_dof("mixed", p_period=2, diag_rebuilt=True)
+    assert base["phase_a"] - drec["phase_a"] == pytest.approx(4 * 5 / 9)
+    assert base["phase_b"] == drec["phase_b"]
+    assert bench.diag_rebuilt(10604322) and not bench.diag_rebuilt(604322)
+    assert not bench.diag_rebuilt(600604183) and not bench.diag_rebuilt(3014062)

@@ -281,7 +281,9 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
 
 # dynamic tasks (ids 1000 VEC + 10 TY + MINB), phase B staged D rows ahead
 # (+ 100000 D), both phases staged (+ 300000 D), phase B filled by bulk copies
-# (+ 2000000), blocks of 6 warps with a run-time task height (+ 600000000), and the
+# (+ 2000000), blocks of 6 warps with a run-time task height (+ 600000000), phase A
+# rebuilding the diagonal from the couplings (+ 10000000; two-row grid: every row
+# carries a Dirichlet face), and the
 # static schedule with phase A marching against phase B
 # (ids 1000000 + 1000 VEC + MINB); float VEC > 1 kernels need n_theta % 4 == 0,
 # double ones an even n_theta, the bulk-copied phase B n_theta >= 136
@@ -292,6 +294,7 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
     (1, 2604322, 136, 45, 9), (1, 2604322, 260, 70, 3), (1, 2604322, 384, 33, 2),
     (1, 600604183, 132, 45, 9), (1, 600604183, 260, 70, 3), (1, 600604323, 132, 45, 9),
     (1, 600604163, 64, 3, 2),
+    (1, 10604322, 132, 45, 9), (1, 10604322, 260, 70, 3), (1, 10604322, 64, 2, 2),
     (1, 1001004, 131, 7, 3), (0, 2322, 130, 45, 9), (0, 1002002, 130, 45, 9),
     (0, 1001003, 131, 7, 3), (0, 1001003, 3, 2, 1),
 ])
@@ -533,6 +536,40 @@ def test_simplified_picard_step_matches_oracle(g, ctx, nth, nz, textured, precis
     g.gmaf_last_fields(ctx, nth, nz, buf)
     hb = host(buf)
     assert np.all(hb[5 * n:] == 7.0) and np.all(np.isfinite(hb[:5 * n]))
+
+
+@pytest.mark.parametrize("scheme", ["general", "simplified"])
+def test_rebuilt_diagonal_picard_step_matches_oracle(g, monkeypatch, scheme):
+    """Phase A rebuilding the diagonal from the couplings (variant 10604322) reads the
+    Dirichlet term of the first and last rows per coefficient slot: 5 slots for the
+    general step's 9 conditions, 1 for the simplified step's 5.  Mixed precision
+    against the oracle's step."""
+    monkeypatch.setenv("GMAF_VARIANT", "10604322")
+    nth, nz = 96, 48
+    tex = tex_dimples()
+    st0 = states(1, seed=31)[0]
+    e_prev = st0[:4] - 2e-8
+    Fext = np.array([25.0, -10.0, 4.0, 3.0])
+    dt, eps = 2.78e-4, 1e-12
+    c = g.Context()
+    try:
+        if scheme == "general":
+            r = g.gmaf_picard_step(c.handle, nth, nz, PHYS, tex, st0, e_prev, dt, Fext, 2e-8, 1e-6,
+                                   g.solver_opts(eps=eps, precision=1))
+            o = oracle.picard_step(nth, nz, PHYS, tex, st0, e_prev, dt, Fext, 2e-8, 1e-6, eps=eps)
+        else:
+            r = g.gmaf_picard_step_simplified(c.handle, nth, nz, PHYS, tex, st0, dt, Fext, 1e-6,
+                                              g.solver_opts(eps=eps, precision=1))
+            o = oracle.picard_step_simplified(nth, nz, PHYS, tex, st0, dt, Fext, 1e-6, eps=eps)
+        info = g.gmaf_last_solve_info(c.handle)
+    finally:
+        c.close()
+    assert info["kernel_variant"] == 10604322
+    assert r["status"] == 0 and o["status"] == 0
+    assert load_err(r["loads"], o["loads"]) <= 1e-5
+    np.testing.assert_allclose(r["G"], o["G"], rtol=1e-6, atol=1e-6 * np.abs(o["G"]).max())
+    ds_g, ds_o = r["state"] - st0, o["state"] - st0
+    assert np.linalg.norm(ds_g - ds_o) <= 1e-4 * np.linalg.norm(ds_o) + 1e-20
 
 
 @pytest.mark.parametrize("precision", [0, 1])
