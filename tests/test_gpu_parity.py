@@ -283,7 +283,8 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
 # (+ 100000 D), both phases staged (+ 300000 D), phase B filled by bulk copies
 # (+ 2000000), blocks of 6 warps with a run-time task height (+ 600000000), phase A
 # rebuilding the diagonal from the couplings (+ 10000000; two-row grid: every row
-# carries a Dirichlet face), and the
+# carries a Dirichlet face; n_theta = 4: one strip wrapped 32 times; 388 x 97: a
+# ragged last strip and a one-row last task), and the
 # static schedule with phase A marching against phase B
 # (ids 1000000 + 1000 VEC + MINB); float VEC > 1 kernels need n_theta % 4 == 0,
 # double ones an even n_theta, the bulk-copied phase B n_theta >= 136
@@ -295,6 +296,7 @@ def test_solve_is_deterministic_and_graph_matches_host_loop(g, monkeypatch):
     (1, 600604183, 132, 45, 9), (1, 600604183, 260, 70, 3), (1, 600604323, 132, 45, 9),
     (1, 600604163, 64, 3, 2),
     (1, 10604322, 132, 45, 9), (1, 10604322, 260, 70, 3), (1, 10604322, 64, 2, 2),
+    (1, 10604322, 4, 3, 1), (1, 10604322, 388, 97, 5),
     (1, 1001004, 131, 7, 3), (0, 2322, 130, 45, 9), (0, 1002002, 130, 45, 9),
     (0, 1001003, 131, 7, 3), (0, 1001003, 3, 2, 1),
 ])
